@@ -1,0 +1,174 @@
+/*
+ * mrpt.h -- C ABI of the GB300 (sm_103a) implementation of multiple random
+ * projection trees with voting (Hyvonen et al., "Fast k-NN search",
+ * arXiv:1509.06957).
+ *
+ * Offline phase (Sec. I-A, Sec. II, Algorithms 1-2): mrpt_build grows T
+ * sparse random projection trees of depth l over n points of dimension d.
+ * Online phase (Sec. III, Algorithms 3-4): mrpt_query routes each query down
+ * every tree, counts votes over the T leaves it lands in, keeps the points
+ * with at least v votes as the candidate set S and returns the k nearest
+ * members of S by Euclidean distance.
+ *
+ * Conventions shared by every entry point:
+ *   - All matrices are row-major, float32, tightly packed (row stride = d).
+ *   - Pointer arguments may be host or device memory of the current CUDA
+ *     device; the library asks the CUDA runtime which.  Device buffers are
+ *     used in place.  Host buffers (pinned or pageable) are staged through
+ *     device buffers owned by the index, and a call that was given any host
+ *     buffer returns only after its results are in that buffer.
+ *   - A call given only device buffers is stream-ordered on the index's
+ *     stream (mrpt_set_stream) and may return before the GPU has finished.
+ *     Errors detected on the device (a non-finite query value) are latched
+ *     in the index and reported by mrpt_sync or by the next call that
+ *     synchronises.
+ *   - Return value: MRPT_OK (0) or a negative MRPT_ERR_* code; after an
+ *     error, mrpt_last_error() gives a message for the calling thread.
+ *   - One index may be used by one host thread at a time, and queries on one
+ *     index run one after another (they share the index's scratch buffers).
+ *   - Ids are int32: n < 2^31.
+ */
+#ifndef MRPT_H
+#define MRPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRPT_OK 0
+#define MRPT_ERR_INVALID_ARG -1      /* a size, parameter or pointer is out of range */
+#define MRPT_ERR_NONFINITE_INPUT -2  /* NaN or Inf in the data or in a query */
+#define MRPT_ERR_OOM -3              /* a device or host allocation failed */
+#define MRPT_ERR_CUDA -4             /* a CUDA runtime call failed */
+#define MRPT_ERR_TIMEOUT -5          /* a bounded device-side wait ran out */
+#define MRPT_ERR_UNSUPPORTED -6      /* valid request outside this build's limits */
+
+/* Limits of this build. */
+#define MRPT_MAX_TREES 255   /* vote counters are 8-bit; F(x;q) <= T (Sec. III-A) */
+#define MRPT_MAX_DEPTH 24    /* 2^l leaves per tree */
+#define MRPT_MAX_K 256       /* neighbours per query */
+#define MRPT_MAX_DIM 32768   /* dimension d */
+
+typedef struct mrpt_index mrpt_index; /* opaque; owned by the library */
+
+/*
+ * mrpt_build -- Algorithm 1 (grow T trees) with Algorithm 2 per tree.
+ *
+ *   data     n x d float32, host or device; copied into memory owned by the
+ *            index, so the caller may free it when the call returns.
+ *   n, d     number of points (2^l <= n < 2^31) and dimension (1..MRPT_MAX_DIM).
+ *   T        number of trees, 1..MRPT_MAX_TREES.
+ *   l        depth, 0..MRPT_MAX_DEPTH, with 2^l <= n.  Leaves hold
+ *            ceil(n/2^l) or floor(n/2^l) points (Sec. III-A).
+ *   density  the paper's sparsity a in (0, 1] (Sec. II-B); each component
+ *            of each level's random vector is N(0,1) with probability a,
+ *            else 0.  a = 1/sqrt(d) is the paper's choice; 0 or a negative
+ *            value selects it.
+ *   seed     key of the counter-based random source: component i of tree
+ *            t's level-j vector takes draws 3((t l + j) d + i) + {0,1,2} of
+ *            SplitMix64 started at `seed` (Bernoulli by u < a, N(0,1) by
+ *            Box-Muller in double, rounded to float).  Trees are therefore
+ *            prefix-stable: the first T trees of a larger index are equal.
+ *   out      receives the new index.
+ *
+ * Points are split at the median of their projections with the order-based
+ * rule of Sec. II-A: sorted by (projection, id), the first ceil(c/2) points
+ * of a node go left and the node's split value is the projection of the
+ * last of them.  Projections are fmaf chains over each vector's nonzeros in
+ * ascending dimension from +0.0f (one rounding per term).
+ * Errors: INVALID_ARG, NONFINITE_INPUT (data holds NaN/Inf), OOM, CUDA.
+ * Synchronous: returns after the index is complete.
+ */
+int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
+               uint64_t seed, mrpt_index **out);
+
+/*
+ * mrpt_query -- Algorithm 4 (with Algorithm 3 per tree) for m queries.
+ *
+ *   Q          m x d float32 queries, host or device.
+ *   m          number of queries, >= 0 (0 is a no-op).
+ *   k          neighbours per query, 1..MRPT_MAX_K.
+ *   v          vote threshold, 1..T: S = {x : F(x;q) >= v} (Sec. III-A).
+ *   out_ids    m x k int32: row i holds query i's neighbours ordered by
+ *              (distance, id) ascending; -1 where |S| < k.
+ *   out_dists  m x k float32 Euclidean distances (Sec. I-A), +inf where
+ *              |S| < k.  Distances are accumulated in float32.
+ * Equivalent to mrpt_query_ex with opts = NULL.
+ * Errors: INVALID_ARG, NONFINITE_INPUT (latched, see above), OOM, CUDA.
+ */
+int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
+               int32_t *out_ids, float *out_dists);
+
+/* Optional controls and debug outputs of mrpt_query_ex.  Zero-initialise
+ * and set what is needed.  Debug pointers are device or host buffers. */
+typedef struct mrpt_query_opts {
+    int32_t n_trees;      /* use the first n_trees trees (0 = all T) */
+    int32_t reserved0;
+    /* debug outputs (NULL = not written) */
+    float *proj;          /* m x (n_trees*l): p = q^T R per tree and level (Algorithm 3) */
+    int32_t *leaf;        /* m x n_trees: the query's leaf in each tree */
+    uint8_t *votes;       /* m x n: F(x;q) per point (Sec. III-A) */
+    int64_t *n_cand;      /* m: |S| */
+    int32_t *cand;        /* m x cand_cap: members of S (any order) */
+    int64_t cand_cap;     /* row capacity of `cand`; members past it are dropped */
+} mrpt_query_opts;
+
+int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
+                  const mrpt_query_opts *opts, int32_t *out_ids, float *out_dists);
+
+/* Release the index and everything it owns.  NULL is accepted. */
+int mrpt_free(mrpt_index *idx);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *mrpt_last_error(void);
+
+/* Stream on which the index's work is ordered (a cudaStream_t; NULL is the
+ * legacy default stream).  Applies to later calls. */
+int mrpt_set_stream(mrpt_index *idx, void *stream);
+
+/* Wait for the index's stream, then report and clear the device-latched
+ * status: MRPT_OK or MRPT_ERR_NONFINITE_INPUT / MRPT_ERR_TIMEOUT. */
+int mrpt_sync(mrpt_index *idx);
+
+/* Shape of an index. */
+typedef struct mrpt_index_info {
+    int64_t n;
+    int32_t d, T, l;
+    float density;
+    uint64_t seed;
+    int64_t nnz;           /* nonzeros of R over all T*l vectors */
+    int64_t device_bytes;  /* device memory held (index + scratch) */
+} mrpt_index_info;
+
+int mrpt_info(const mrpt_index *idx, mrpt_index_info *info);
+
+/* Index contents, for inspection and tests. */
+enum mrpt_export_what {
+    MRPT_EXPORT_R_COL_OFF = 0, /* int32 [T*l+1] column offsets of R (column t*l+j) */
+    MRPT_EXPORT_R_DIM = 1,     /* int32 [nnz] dimension of each nonzero, ascending per column */
+    MRPT_EXPORT_R_VAL = 2,     /* float32 [nnz] value of each nonzero */
+    MRPT_EXPORT_SPLIT = 3,     /* float32 [T][2^l-1] split values, heap order per tree */
+    MRPT_EXPORT_LEAF_OFF = 4,  /* int32 [T][2^l+1] leaf offsets into LEAF_IDS rows */
+    MRPT_EXPORT_LEAF_IDS = 5,  /* int32 [T][n] point ids, leaves left to right, ids ascending */
+    MRPT_EXPORT_DATA = 6       /* float32 [n][d] the index's copy of the data */
+};
+
+/* Bytes that mrpt_export writes for `what` (negative error code if invalid). */
+int64_t mrpt_export_size(const mrpt_index *idx, int32_t what);
+
+/* Copy `what` into dst (host or device, dst_bytes >= mrpt_export_size).
+ * Synchronous. */
+int mrpt_export(const mrpt_index *idx, int32_t what, void *dst, int64_t dst_bytes);
+
+/* Fault injection for tests: make the allocation after the next `after`
+ * successful ones fail with MRPT_ERR_OOM (negative disables).  Host-side
+ * only; process-wide. */
+int mrpt_debug_fail_alloc_after(int32_t after);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRPT_H */

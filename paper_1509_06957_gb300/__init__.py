@@ -1,0 +1,340 @@
+"""GB300 (sm_103a) multiple random projection trees with voting.
+
+Thin Python binding of the C ABI in ``include/mrpt.h`` (library
+``_build/libmrpt.so``, built from ``csrc/`` by :mod:`.build`).  Every step
+of index construction and of the query runs in the library's CUDA kernels;
+this module only marshals arguments: it passes raw pointers of torch tensors
+(device memory, current stream) or numpy arrays (host memory) and turns
+error codes into exceptions.  There is no CPU fallback: if the library is
+missing or a call fails, an exception is raised.
+
+Names follow the C ABI: :func:`mrpt_build`, :func:`mrpt_query`,
+:func:`mrpt_query_ex`, :func:`mrpt_free`, :func:`mrpt_last_error`,
+:func:`mrpt_set_stream`, :func:`mrpt_sync`, :func:`mrpt_info`,
+:func:`mrpt_export`, plus the :class:`Index` handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MRPT_OK = 0
+MRPT_ERR_INVALID_ARG = -1
+MRPT_ERR_NONFINITE_INPUT = -2
+MRPT_ERR_OOM = -3
+MRPT_ERR_CUDA = -4
+MRPT_ERR_TIMEOUT = -5
+MRPT_ERR_UNSUPPORTED = -6
+
+MRPT_MAX_TREES = 255
+MRPT_MAX_DEPTH = 24
+MRPT_MAX_K = 256
+MRPT_MAX_DIM = 32768
+
+EXPORT = {
+    "R_COL_OFF": (0, np.int32),
+    "R_DIM": (1, np.int32),
+    "R_VAL": (2, np.float32),
+    "SPLIT": (3, np.float32),
+    "LEAF_OFF": (4, np.int32),
+    "LEAF_IDS": (5, np.int32),
+    "DATA": (6, np.float32),
+}
+
+#: every symbol include/mrpt.h declares
+ABI_SYMBOLS = (
+    "mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
+    "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
+    "mrpt_debug_fail_alloc_after",
+)
+
+
+class MRPTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class QueryOpts(ctypes.Structure):
+    _fields_ = [
+        ("n_trees", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("proj", ctypes.c_void_p),
+        ("leaf", ctypes.c_void_p),
+        ("votes", ctypes.c_void_p),
+        ("n_cand", ctypes.c_void_p),
+        ("cand", ctypes.c_void_p),
+        ("cand_cap", ctypes.c_int64),
+    ]
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("l", ctypes.c_int32),
+        ("density", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+        ("nnz", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libmrpt.so (building it first when it is missing or stale and
+    nvcc is available).  Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build_library()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmrpt.so not found at {path}; run paper_1509_06957_gb300.build")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        lib.mrpt_build.restype = ctypes.c_int
+        lib.mrpt_build.argtypes = [vp, i64, i32, i32, i32, f32, ctypes.c_uint64,
+                                   ctypes.POINTER(vp)]
+        lib.mrpt_query.restype = ctypes.c_int
+        lib.mrpt_query.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        lib.mrpt_query_ex.restype = ctypes.c_int
+        lib.mrpt_query_ex.argtypes = [vp, vp, i64, i32, i32, ctypes.POINTER(QueryOpts), vp, vp]
+        lib.mrpt_free.restype = ctypes.c_int
+        lib.mrpt_free.argtypes = [vp]
+        lib.mrpt_last_error.restype = ctypes.c_char_p
+        lib.mrpt_last_error.argtypes = []
+        lib.mrpt_set_stream.restype = ctypes.c_int
+        lib.mrpt_set_stream.argtypes = [vp, vp]
+        lib.mrpt_sync.restype = ctypes.c_int
+        lib.mrpt_sync.argtypes = [vp]
+        lib.mrpt_info.restype = ctypes.c_int
+        lib.mrpt_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+        lib.mrpt_export_size.restype = ctypes.c_int64
+        lib.mrpt_export_size.argtypes = [vp, i32]
+        lib.mrpt_export.restype = ctypes.c_int
+        lib.mrpt_export.argtypes = [vp, i32, vp, i64]
+        lib.mrpt_debug_fail_alloc_after.restype = ctypes.c_int
+        lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
+        _lib = lib
+        return lib
+
+
+def mrpt_last_error() -> str:
+    return load_library().mrpt_last_error().decode(errors="replace")
+
+
+def _check(rc: int) -> None:
+    if rc != MRPT_OK:
+        raise MRPTError(rc, mrpt_last_error())
+
+
+# ------------------------------------------------------------ marshalling --
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    assert x.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _current_stream(x):
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return None
+
+
+def _as_f32(x):
+    if _is_torch(x):
+        import torch
+        return x.to(torch.float32).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def _empty_like_input(x, shape, dtype):
+    """Output buffer on the same side (device/host) as the input `x`."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.int32: torch.int32, np.float32: torch.float32, np.uint8: torch.uint8,
+               np.int64: torch.int64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=x.device)
+    return np.empty(shape, dtype=dtype)
+
+
+class Index:
+    """Handle of an index built by :func:`mrpt_build`; freed on close()."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        self._lib = load_library()
+        info = IndexInfo()
+        _check(self._lib.mrpt_info(self._h, ctypes.byref(info)))
+        self.n, self.d, self.T, self.l = info.n, info.d, info.T, info.l
+        self.density, self.seed, self.nnz = info.density, info.seed, info.nnz
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("index is closed")
+        return self._h
+
+    def info(self) -> IndexInfo:
+        return mrpt_info(self)
+
+    def query(self, Q, k: int, v: int, **kw):
+        return mrpt_query(self, Q, k, v, **kw)
+
+    def export(self, what: str):
+        return mrpt_export(self, what)
+
+    def close(self):
+        if self._h is not None:
+            _check(self._lib.mrpt_free(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0) -> Index:
+    """Algorithm 1: grow T trees of depth l over the rows of ``data`` (torch
+    tensor on the GPU or the host, or a numpy array)."""
+    lib = load_library()
+    data = _as_f32(data)
+    n, d = data.shape
+    h = ctypes.c_void_p()
+    _check(lib.mrpt_build(_ptr(data), n, d, T, l, float(density), seed & (2**64 - 1),
+                          ctypes.byref(h)))
+    if _is_torch(data) and data.is_cuda:
+        # mrpt_build copies the data; keep the source alive until it returns (it is synchronous)
+        pass
+    return Index(h)
+
+
+def mrpt_free(index: Index) -> None:
+    index.close()
+
+
+def mrpt_set_stream(index: Index, stream) -> None:
+    """Order the index's work on ``stream`` (torch.cuda.Stream, raw handle or None)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load_library().mrpt_set_stream(index.handle, ctypes.c_void_p(stream)))
+
+
+def mrpt_sync(index: Index) -> None:
+    _check(load_library().mrpt_sync(index.handle))
+
+
+def mrpt_info(index: Index) -> IndexInfo:
+    info = IndexInfo()
+    _check(load_library().mrpt_info(index.handle, ctypes.byref(info)))
+    return info
+
+
+def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
+                  out_dists=None, debug: bool = False, cand_cap: int | None = None):
+    """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
+    tensors for a CUDA tensor, numpy arrays for host input) unless given.
+    With ``debug`` also returns a dict of the internals: proj, leaf, votes,
+    n_cand and cand (members of S, row padded)."""
+    lib = load_library()
+    Q = _as_f32(Q)
+    m = Q.shape[0]
+    if out_ids is None:
+        out_ids = _empty_like_input(Q, (m, k), np.int32)
+    if out_dists is None:
+        out_dists = _empty_like_input(Q, (m, k), np.float32)
+    stream = _current_stream(Q)
+    if stream is not None:
+        _check(lib.mrpt_set_stream(index.handle, stream))
+    opts = QueryOpts()
+    opts.n_trees = int(n_trees)
+    dbg = None
+    if debug:
+        T_use = n_trees if n_trees > 0 else index.T
+        cap = cand_cap if cand_cap is not None else index.n
+        dbg = {
+            "proj": _empty_like_input(Q, (m, T_use * index.l), np.float32),
+            "leaf": _empty_like_input(Q, (m, T_use), np.int32),
+            "votes": _empty_like_input(Q, (m, index.n), np.uint8),
+            "n_cand": _empty_like_input(Q, (m,), np.int64),
+            "cand": _empty_like_input(Q, (m, max(cap, 1)), np.int32),
+        }
+        opts.proj = _ptr(dbg["proj"]).value
+        opts.leaf = _ptr(dbg["leaf"]).value
+        opts.votes = _ptr(dbg["votes"]).value
+        opts.n_cand = _ptr(dbg["n_cand"]).value
+        opts.cand = _ptr(dbg["cand"]).value
+        opts.cand_cap = max(cap, 1)
+    _check(lib.mrpt_query_ex(index.handle, _ptr(Q), m, k, v, ctypes.byref(opts), _ptr(out_ids),
+                             _ptr(out_dists)))
+    if debug:
+        return out_ids, out_dists, dbg
+    return out_ids, out_dists
+
+
+def mrpt_query(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
+               out_dists=None):
+    """Algorithm 4: k approximate nearest neighbours of each row of Q."""
+    return mrpt_query_ex(index, Q, k, v, n_trees=n_trees, out_ids=out_ids,
+                         out_dists=out_dists)
+
+
+def mrpt_export(index: Index, what: str) -> np.ndarray:
+    """Copy one part of the index to a host numpy array (see mrpt.h)."""
+    lib = load_library()
+    code, dt = EXPORT[what]
+    nbytes = lib.mrpt_export_size(index.handle, code)
+    if nbytes < 0:
+        _check(int(nbytes))
+    out = np.empty(max(nbytes, 1) // np.dtype(dt).itemsize, dtype=dt)
+    _check(lib.mrpt_export(index.handle, code, ctypes.c_void_p(out.ctypes.data), out.nbytes))
+    out = out[: nbytes // np.dtype(dt).itemsize]
+    L = 1 << index.l
+    if what == "SPLIT":
+        return out.reshape(index.T, L - 1)
+    if what == "LEAF_OFF":
+        return out.reshape(index.T, L + 1)
+    if what == "LEAF_IDS":
+        return out.reshape(index.T, index.n)
+    if what == "DATA":
+        return out.reshape(index.n, index.d)
+    return out
+
+
+def mrpt_debug_fail_alloc_after(after: int) -> None:
+    _check(load_library().mrpt_debug_fail_alloc_after(int(after)))

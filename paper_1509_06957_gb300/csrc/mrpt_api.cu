@@ -1,0 +1,436 @@
+// C ABI (include/mrpt.h): argument checks, ownership, host/device staging.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "mrpt_internal.cuh"
+
+namespace mrpt {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<int32_t> g_fail_after{-1};
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return MRPT_ERR_CUDA;
+}
+
+static bool take_injected_failure() {
+    int32_t cur = g_fail_after.load();
+    while (cur >= 0) {
+        if (g_fail_after.compare_exchange_weak(cur, cur - 1)) return cur == 0;
+    }
+    return false;
+}
+
+int dev_alloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (take_injected_failure()) {
+        set_error(std::string("out of device memory (injected) allocating ") + what);
+        return MRPT_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error(std::string("out of device memory allocating ") + what + " (" +
+                  std::to_string(bytes) + " bytes)");
+        return MRPT_ERR_OOM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return MRPT_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int Scratch::ensure(size_t need, const char *what) {
+    if (need <= bytes && ptr != nullptr) return MRPT_OK;
+    release();
+    size_t cap = need < 4096 ? 4096 : need + need / 4;
+    int rc = dev_alloc(&ptr, cap, what);
+    if (rc) return rc;
+    bytes = cap;
+    return MRPT_OK;
+}
+
+void Scratch::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+static void free_index(mrpt_index *idx) {
+    if (!idx) return;
+    cudaFree(idx->X);
+    cudaFree(idx->col_off);
+    cudaFree(idx->dim);
+    cudaFree(idx->val);
+    cudaFree(idx->split);
+    cudaFree(idx->leaf_off);
+    cudaFree(idx->leaf_ids);
+    cudaFree(idx->status);
+    idx->q_leaf.release();
+    idx->q_stage.release();
+    idx->o_stage.release();
+    idx->dbg_stage.release();
+    delete idx;
+}
+
+}  // namespace mrpt
+
+using namespace mrpt;
+
+extern "C" {
+
+const char *mrpt_last_error(void) { return g_last_error.c_str(); }
+
+int mrpt_debug_fail_alloc_after(int32_t after) {
+    g_fail_after.store(after < 0 ? -1 : after);
+    return MRPT_OK;
+}
+
+int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
+               uint64_t seed, mrpt_index **out) {
+    clear_error();
+    if (!out) {
+        set_error("mrpt_build: out is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!data || n < 1 || n > int64_t(INT32_MAX) || d < 1 || d > MRPT_MAX_DIM || T < 1 ||
+        T > MRPT_MAX_TREES || l < 0 || l > MRPT_MAX_DEPTH || (int64_t(1) << l) > n ||
+        !(density <= 1.0f) || std::isnan(density)) {
+        set_error("mrpt_build: invalid argument (need data != NULL, 1 <= n < 2^31, 1 <= d <= " +
+                  std::to_string(MRPT_MAX_DIM) + ", 1 <= T <= " + std::to_string(MRPT_MAX_TREES) +
+                  ", 0 <= l <= " + std::to_string(MRPT_MAX_DEPTH) +
+                  ", 2^l <= n, density <= 1)");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (density <= 0.0f) density = float(1.0 / std::sqrt(double(d)));
+
+    mrpt_index *idx = new (std::nothrow) mrpt_index();
+    if (!idx) {
+        set_error("mrpt_build: host allocation failed");
+        return MRPT_ERR_OOM;
+    }
+    int rc = MRPT_OK;
+    cudaGetDevice(&idx->device);
+    idx->n = n;
+    idx->d = d;
+    idx->dpad = (d + 7) & ~7;
+    idx->T = T;
+    idx->l = l;
+    idx->L = int64_t(1) << l;
+    idx->density = density;
+    idx->seed = seed;
+    idx->stream = nullptr;
+    cudaStream_t s = idx->stream;
+
+    auto fail = [&](int code) {
+        free_index(idx);
+        return code;
+    };
+
+    // ---- data: n x dpad, zero padded
+    const size_t xbytes = size_t(n) * size_t(idx->dpad) * sizeof(float);
+    if ((rc = dev_alloc((void **)&idx->X, xbytes, "index data"))) return fail(rc);
+    idx->device_bytes += int64_t(xbytes);
+    {
+        cudaError_t e = cudaMemsetAsync(idx->X, 0, xbytes, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(idx->X, size_t(idx->dpad) * sizeof(float), data,
+                                  size_t(d) * sizeof(float), size_t(d) * sizeof(float), size_t(n),
+                                  cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: copying data"));
+    }
+    bool nonfinite = false;
+    if ((rc = check_finite(idx->X, n, idx->dpad, d, s, &nonfinite))) return fail(rc);
+    if (nonfinite) {
+        set_error("mrpt_build: data holds NaN or Inf");
+        return fail(MRPT_ERR_NONFINITE_INPUT);
+    }
+
+    // ---- random matrix (Algorithm 1, Sec. II-B/II-C)
+    generate_random_matrix(T, l, d, density, seed, idx->h_col_off, idx->h_dim, idx->h_val);
+    idx->nnz = int64_t(idx->h_dim.size());
+    const size_t cbytes = idx->h_col_off.size() * sizeof(int32_t);
+    const size_t nbytes = size_t(idx->nnz) * sizeof(int32_t);
+    if ((rc = dev_alloc((void **)&idx->col_off, cbytes, "R column offsets"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&idx->dim, nbytes, "R dimensions"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&idx->val, nbytes, "R values"))) return fail(rc);
+    idx->device_bytes += int64_t(cbytes + 2 * nbytes);
+    {
+        cudaError_t e = cudaMemcpy(idx->col_off, idx->h_col_off.data(), cbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nbytes)
+            e = cudaMemcpy(idx->dim, idx->h_dim.data(), nbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nbytes)
+            e = cudaMemcpy(idx->val, idx->h_val.data(), nbytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: uploading R"));
+    }
+
+    // ---- trees (Algorithm 2)
+    const size_t sbytes = size_t(T) * size_t(idx->L - 1) * sizeof(float);
+    if ((rc = dev_alloc((void **)&idx->split, sbytes, "split values"))) return fail(rc);
+    if ((rc = dev_alloc((void **)&idx->leaf_off, size_t(idx->L + 1) * sizeof(int32_t), "leaf offsets")))
+        return fail(rc);
+    if ((rc = dev_alloc((void **)&idx->status, 4 * sizeof(uint32_t), "status words"))) return fail(rc);
+    idx->device_bytes += int64_t(sbytes + size_t(idx->L + 1) * 4 + 16);
+    {
+        cudaError_t e = cudaMemset(idx->status, 0, 4 * sizeof(uint32_t));
+        if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: status"));
+    }
+    if ((rc = grow_trees_device(idx))) return fail(rc);
+    *out = idx;
+    return MRPT_OK;
+}
+
+int mrpt_free(mrpt_index *idx) {
+    clear_error();
+    if (idx) {
+        cudaStreamSynchronize(idx->stream);
+        free_index(idx);
+    }
+    return MRPT_OK;
+}
+
+int mrpt_set_stream(mrpt_index *idx, void *stream) {
+    clear_error();
+    if (!idx) {
+        set_error("mrpt_set_stream: idx is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    idx->stream = static_cast<cudaStream_t>(stream);
+    return MRPT_OK;
+}
+
+int mrpt_sync(mrpt_index *idx) {
+    clear_error();
+    if (!idx) {
+        set_error("mrpt_sync: idx is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, idx->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, idx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+    if (e == cudaSuccess && st) e = cudaMemsetAsync(idx->status, 0, sizeof(uint32_t), idx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mrpt_sync");
+    if (st & STATUS_TIMEOUT) {
+        set_error("a bounded device wait ran out");
+        return MRPT_ERR_TIMEOUT;
+    }
+    if (st & STATUS_NONFINITE_QUERY) {
+        set_error("a query held NaN or Inf");
+        return MRPT_ERR_NONFINITE_INPUT;
+    }
+    return MRPT_OK;
+}
+
+int mrpt_info(const mrpt_index *idx, mrpt_index_info *info) {
+    clear_error();
+    if (!idx || !info) {
+        set_error("mrpt_info: NULL argument");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    info->n = idx->n;
+    info->d = idx->d;
+    info->T = idx->T;
+    info->l = idx->l;
+    info->density = idx->density;
+    info->seed = idx->seed;
+    info->nnz = idx->nnz;
+    info->device_bytes = idx->device_bytes + int64_t(idx->q_leaf.bytes + idx->q_stage.bytes +
+                                                     idx->o_stage.bytes + idx->dbg_stage.bytes);
+    return MRPT_OK;
+}
+
+int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
+                  const mrpt_query_opts *opts, int32_t *out_ids, float *out_dists) {
+    clear_error();
+    if (!idx) {
+        set_error("mrpt_query: idx is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    const int32_t n_trees = (opts && opts->n_trees > 0) ? opts->n_trees : idx->T;
+    if (m < 0 || (m > 0 && (!Q || !out_ids || !out_dists)) || k < 1 || k > MRPT_MAX_K || v < 1 ||
+        n_trees > idx->T || v > n_trees) {
+        set_error("mrpt_query: invalid argument (need m >= 0, non-NULL buffers, 1 <= k <= " +
+                  std::to_string(MRPT_MAX_K) + ", 1 <= v <= n_trees <= T)");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (opts && opts->cand && opts->cand_cap < 0) {
+        set_error("mrpt_query: cand_cap < 0");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (m == 0) return MRPT_OK;
+    cudaStream_t s = idx->stream;
+    int rc;
+    bool any_host = false;
+
+    // ---- inputs
+    const float *Qd = Q;
+    if (!is_device_ptr(Q)) {
+        any_host = true;
+        const size_t qb = size_t(m) * size_t(idx->d) * sizeof(float);
+        if ((rc = idx->q_stage.ensure(qb, "query staging"))) return rc;
+        MRPT_CUDA_TRY(cudaMemcpyAsync(idx->q_stage.ptr, Q, qb, cudaMemcpyHostToDevice, s));
+        Qd = static_cast<const float *>(idx->q_stage.ptr);
+    }
+    // ---- outputs (device buffers in place, host buffers staged)
+    const bool ids_dev = is_device_ptr(out_ids);
+    const bool dists_dev = is_device_ptr(out_dists);
+    const size_t ob = size_t(m) * size_t(k) * 4;
+    if (!ids_dev || !dists_dev) {
+        any_host = true;
+        if ((rc = idx->o_stage.ensure(2 * ob, "output staging"))) return rc;
+    }
+    int32_t *ids_d = ids_dev ? out_ids : static_cast<int32_t *>(idx->o_stage.ptr);
+    float *dists_d = dists_dev ? out_dists
+                               : reinterpret_cast<float *>(static_cast<char *>(idx->o_stage.ptr) + ob);
+
+    // ---- debug outputs (staged when on the host)
+    QueryLaunch ql{};
+    ql.Q = Qd;
+    ql.m = m;
+    ql.k = k;
+    ql.v = v;
+    ql.n_trees = n_trees;
+    ql.out_ids = ids_d;
+    ql.out_dists = dists_d;
+    const size_t leaf_b = size_t(m) * size_t(n_trees) * 4;
+    struct Dbg {
+        void *user;
+        size_t bytes;
+        size_t off;
+    } dbg[5] = {};
+    size_t dbg_total = 0;
+    if (opts) {
+        void *ptrs[5] = {opts->proj, opts->leaf, opts->votes, opts->n_cand, opts->cand};
+        size_t sizes[5] = {size_t(m) * size_t(n_trees) * size_t(idx->l) * 4, leaf_b,
+                           size_t(m) * size_t(idx->n), size_t(m) * 8,
+                           size_t(m) * size_t(opts->cand_cap) * 4};
+        for (int i = 0; i < 5; ++i) {
+            dbg[i].user = ptrs[i];
+            dbg[i].bytes = sizes[i];
+            if (ptrs[i] && !is_device_ptr(ptrs[i])) {
+                dbg[i].off = dbg_total;
+                dbg_total += (sizes[i] + 255) & ~size_t(255);
+                any_host = true;
+            } else {
+                dbg[i].off = SIZE_MAX;
+            }
+        }
+        if (dbg_total && (rc = idx->dbg_stage.ensure(dbg_total, "debug staging"))) return rc;
+        auto dev_of = [&](int i) -> void * {
+            if (!dbg[i].user) return nullptr;
+            if (dbg[i].off == SIZE_MAX) return dbg[i].user;
+            return static_cast<char *>(idx->dbg_stage.ptr) + dbg[i].off;
+        };
+        ql.proj = static_cast<float *>(dev_of(0));
+        ql.leaf = static_cast<int32_t *>(dev_of(1));
+        ql.votes = static_cast<uint8_t *>(dev_of(2));
+        ql.n_cand = static_cast<int64_t *>(dev_of(3));
+        ql.cand = static_cast<int32_t *>(dev_of(4));
+        ql.cand_cap = opts->cand_cap;
+    }
+    if (!ql.leaf) {
+        if ((rc = idx->q_leaf.ensure(leaf_b, "leaf-of-query scratch"))) return rc;
+        ql.leaf = static_cast<int32_t *>(idx->q_leaf.ptr);
+    }
+
+    if ((rc = launch_query(idx, ql))) return rc;
+
+    // ---- copy staged results back
+    if (!ids_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_ids, ids_d, ob, cudaMemcpyDeviceToHost, s));
+    if (!dists_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_dists, dists_d, ob, cudaMemcpyDeviceToHost, s));
+    for (int i = 0; i < 5; ++i)
+        if (dbg[i].user && dbg[i].off != SIZE_MAX)
+            MRPT_CUDA_TRY(cudaMemcpyAsync(dbg[i].user, static_cast<char *>(idx->dbg_stage.ptr) + dbg[i].off,
+                                          dbg[i].bytes, cudaMemcpyDeviceToHost, s));
+    if (any_host) return mrpt_sync(idx);
+    return MRPT_OK;
+}
+
+int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v, int32_t *out_ids,
+               float *out_dists) {
+    return mrpt_query_ex(idx, Q, m, k, v, nullptr, out_ids, out_dists);
+}
+
+int64_t mrpt_export_size(const mrpt_index *idx, int32_t what) {
+    clear_error();
+    if (!idx) {
+        set_error("mrpt_export_size: idx is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    switch (what) {
+        case MRPT_EXPORT_R_COL_OFF: return int64_t(idx->h_col_off.size()) * 4;
+        case MRPT_EXPORT_R_DIM: return idx->nnz * 4;
+        case MRPT_EXPORT_R_VAL: return idx->nnz * 4;
+        case MRPT_EXPORT_SPLIT: return int64_t(idx->T) * (idx->L - 1) * 4;
+        case MRPT_EXPORT_LEAF_OFF: return int64_t(idx->T) * (idx->L + 1) * 4;
+        case MRPT_EXPORT_LEAF_IDS: return int64_t(idx->T) * idx->n * 4;
+        case MRPT_EXPORT_DATA: return idx->n * int64_t(idx->d) * 4;
+        default: break;
+    }
+    set_error("mrpt_export_size: unknown item");
+    return MRPT_ERR_INVALID_ARG;
+}
+
+int mrpt_export(const mrpt_index *idx, int32_t what, void *dst, int64_t dst_bytes) {
+    const int64_t need = mrpt_export_size(idx, what);
+    if (need < 0) return int(need);
+    if (!dst || dst_bytes < need) {
+        set_error("mrpt_export: dst is NULL or too small");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaStreamSynchronize(idx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mrpt_export");
+    switch (what) {
+        case MRPT_EXPORT_R_COL_OFF:
+            e = cudaMemcpy(dst, idx->h_col_off.data(), size_t(need), cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_R_DIM:
+            if (need) e = cudaMemcpy(dst, idx->h_dim.data(), size_t(need), cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_R_VAL:
+            if (need) e = cudaMemcpy(dst, idx->h_val.data(), size_t(need), cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_SPLIT:
+            if (need) e = cudaMemcpy(dst, idx->split, size_t(need), cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_LEAF_OFF:
+            for (int32_t t = 0; t < idx->T && e == cudaSuccess; ++t)
+                e = cudaMemcpy(static_cast<char *>(dst) + size_t(t) * size_t(idx->L + 1) * 4,
+                               idx->leaf_off, size_t(idx->L + 1) * 4, cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_LEAF_IDS:
+            e = cudaMemcpy(dst, idx->leaf_ids, size_t(need), cudaMemcpyDefault);
+            break;
+        case MRPT_EXPORT_DATA:
+            e = cudaMemcpy2D(dst, size_t(idx->d) * 4, idx->X, size_t(idx->dpad) * 4,
+                             size_t(idx->d) * 4, size_t(idx->n), cudaMemcpyDefault);
+            break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mrpt_export");
+    return MRPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mrpt.h"
+
+namespace mrpt {
+
+// ------------------------------------------------------------------ errors --
+
+void set_error(const std::string &msg);
+void clear_error();
+
+// Returns MRPT_ERR_CUDA (and records where) when `e` is not cudaSuccess.
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MRPT_CUDA_TRY(call)                                          \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return ::mrpt::cuda_fail(_e, #call);  \
+    } while (0)
+
+// Device allocation through one gate so that tests can inject failures.
+int dev_alloc(void **p, size_t bytes, const char *what);
+
+// True when `p` is memory of some CUDA device (not host memory).
+bool is_device_ptr(const void *p);
+
+// Grow-only device scratch buffer.
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need, const char *what);
+    void release();
+};
+
+// Device-latched status bits (index->status[0]).
+enum : uint32_t {
+    STATUS_NONFINITE_QUERY = 1u,
+    STATUS_TIMEOUT = 2u,
+};
+
+}  // namespace mrpt
+
+// The index.  Device arrays are owned; see mrpt.h for their meaning.
+struct mrpt_index {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t dpad = 0;       // row stride of X in elements (multiple of 8)
+    int32_t T = 0, l = 0;
+    int64_t L = 1;          // leaves per tree
+    float density = 0.f;
+    uint64_t seed = 0;
+    int64_t nnz = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    float *X = nullptr;          // n x dpad, zero padded
+    int32_t *col_off = nullptr;  // T*l + 1
+    int32_t *dim = nullptr;      // nnz
+    float *val = nullptr;        // nnz
+    float *split = nullptr;      // T x (L-1)
+    int32_t *leaf_off = nullptr; // L + 1 (identical for every tree)
+    int32_t *leaf_ids = nullptr; // T x n
+    uint32_t *status = nullptr;  // [0] latched status bits, [1] work counter
+
+    std::vector<int32_t> h_col_off, h_dim;
+    std::vector<float> h_val;
+
+    // query scratch
+    mrpt::Scratch q_leaf;    // m x T int32
+    mrpt::Scratch q_stage;   // staged host queries (m x d)
+    mrpt::Scratch o_stage;   // staged outputs (m x k ids + m x k dists)
+    mrpt::Scratch dbg_stage; // staged debug outputs
+
+    int64_t device_bytes = 0;
+};
+
+namespace mrpt {
+
+// ------------------------------------------------------ build (mrpt_build.cu)
+
+// Random matrix of Algorithm 1 on the host (counter-based SplitMix64 +
+// Box-Muller); compressed columns, column c = t*l + j.
+void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
+                            std::vector<int32_t> &col_off, std::vector<int32_t> &dim,
+                            std::vector<float> &val);
+
+// Projections and median splits for every tree; fills idx->split,
+// idx->leaf_off and idx->leaf_ids.  X, R must already be on the device.
+int grow_trees_device(mrpt_index *idx);
+
+// Sets *nonfinite when the n x dpad matrix X holds NaN/Inf.
+int check_finite(const float *X, int64_t rows, int32_t stride, int32_t cols, cudaStream_t s,
+                 bool *nonfinite);
+
+// ------------------------------------------------------ query (mrpt_query.cu)
+
+struct QueryLaunch {
+    const float *Q;        // m x d device queries
+    int64_t m;
+    int32_t k, v, n_trees;
+    int32_t *out_ids;      // m x k device
+    float *out_dists;      // m x k device
+    float *proj;           // optional m x (n_trees*l)
+    int32_t *leaf;         // m x n_trees device (scratch or debug)
+    uint8_t *votes;        // optional m x n
+    int64_t *n_cand;       // optional m
+    int32_t *cand;         // optional m x cand_cap
+    int64_t cand_cap;
+};
+
+int launch_query(mrpt_index *idx, const QueryLaunch &ql);
+
+}  // namespace mrpt

@@ -1,0 +1,463 @@
+// Query phase (Sec. III, Algorithms 3-4) on sm_103a.
+//
+//   k_query_route   p = q^T R for every tree and level (Algorithm 3, line
+//                   "p <- q^T R"), then the descent p[level] <= split -> left.
+//                   A block stages a tile of queries in shared memory; one
+//                   thread owns one tree for every query of the tile.
+//   k_vote_search   persistent blocks take queries from an atomic counter.
+//                   Per query: 8-bit vote counters for a chunk of point ids
+//                   in shared memory, incremented by warp-wide passes over
+//                   each tree's leaf (Algorithm 4's vote loop); points with
+//                   at least v votes are compacted into a candidate buffer
+//                   (S of Sec. III-A); a warp per candidate computes the
+//                   float32 squared distance with 128-bit loads and keeps a
+//                   per-warp sorted top-k in registers; the warps' lists are
+//                   merged by rank (knn(q, k, S) of Algorithm 4).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "mrpt_internal.cuh"
+
+namespace mrpt {
+
+// ------------------------------------------------------------- routing ----
+
+template <int QT>
+__global__ void __launch_bounds__(128) k_query_route(
+    const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
+    const int32_t *__restrict__ col_off, const int32_t *__restrict__ dim,
+    const float *__restrict__ val, const float *__restrict__ split, int32_t *__restrict__ leaf,
+    float *__restrict__ proj, uint32_t *__restrict__ status) {
+    extern __shared__ float qs[];  // QT x d
+    const int64_t q0 = int64_t(blockIdx.x) * QT;
+    const int nq = int((m - q0) < QT ? (m - q0) : int64_t(QT));
+    bool bad = false;
+    for (int i = threadIdx.x; i < QT * d; i += blockDim.x) {
+        const int r = i / d;
+        float x = 0.f;
+        if (r < nq) {
+            x = Q[q0 * d + i];
+            bad |= !isfinite(x);
+        }
+        qs[i] = x;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, STATUS_NONFINITE_QUERY);
+    __syncthreads();
+    const int t = blockIdx.y * blockDim.x + threadIdx.x;
+    if (t >= T_use) return;
+    const int64_t inner = L - 1;
+    const float *sp = split + int64_t(t) * inner;
+    int32_t node[QT];
+#pragma unroll
+    for (int q = 0; q < QT; ++q) node[q] = 0;
+    const int ncols = T_use * l;
+    for (int j = 0; j < l; ++j) {
+        const int c = t * l + j;
+        float acc[QT];
+#pragma unroll
+        for (int q = 0; q < QT; ++q) acc[q] = 0.0f;
+        const int e1 = col_off[c + 1];
+        for (int e = col_off[c]; e < e1; ++e) {
+            const int dd = dim[e];
+            const float vv = val[e];
+#pragma unroll
+            for (int q = 0; q < QT; ++q) acc[q] = __fmaf_rn(qs[q * d + dd], vv, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < QT; ++q) {
+            if (proj != nullptr && q < nq) proj[(q0 + q) * ncols + c] = acc[q];
+            node[q] = 2 * node[q] + 1 + (acc[q] > sp[node[q]] ? 1 : 0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QT; ++q)
+        if (q < nq) leaf[(q0 + q) * T_use + t] = int32_t(node[q] - inner);
+}
+
+// ---------------------------------------------------------- vote search ----
+
+constexpr int VS_THREADS = 512;
+constexpr int VS_WARPS = VS_THREADS / 32;
+constexpr int CH_WORDS = 16384;          // 64 KB: 8-bit counters for 65,536 ids
+constexpr int64_t CH_IDS = int64_t(CH_WORDS) * 4;
+constexpr int CAND_BUF = 4096;           // candidate ids buffered per batch
+constexpr int32_t SENTINEL_ID = 0x7fffffff;
+
+__device__ __forceinline__ bool pair_less(float da, int32_t ia, float db, int32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// A warp's k smallest (distance, id) pairs, sorted ascending; entry
+// r*32 + lane lives in lane `lane`, slot r.
+template <int KR>
+struct WarpTopK {
+    float d[KR];
+    int32_t i[KR];
+    float thr_d;
+    int32_t thr_i;
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+            d[r] = INFINITY;
+            i[r] = SENTINEL_ID;
+        }
+        thr_d = INFINITY;
+        thr_i = SENTINEL_ID;
+    }
+
+    // nd/ni are warp-uniform.
+    __device__ __forceinline__ void insert(float nd, int32_t ni, int k, int lane) {
+        if (!pair_less(nd, ni, thr_d, thr_i)) return;
+        int pos = 0;
+#pragma unroll
+        for (int r = 0; r < KR; ++r)
+            pos += __popc(__ballot_sync(0xffffffffu, pair_less(d[r], i[r], nd, ni)));
+#pragma unroll
+        for (int r = KR - 1; r >= 0; --r) {
+            float ud = __shfl_up_sync(0xffffffffu, d[r], 1);
+            int32_t ui = __shfl_up_sync(0xffffffffu, i[r], 1);
+            float pd = INFINITY;
+            int32_t pi = SENTINEL_ID;
+            if (r > 0) {
+                pd = __shfl_sync(0xffffffffu, d[r > 0 ? r - 1 : 0], 31);
+                pi = __shfl_sync(0xffffffffu, i[r > 0 ? r - 1 : 0], 31);
+            }
+            if (lane == 0) {
+                ud = pd;
+                ui = pi;
+            }
+            const int e = r * 32 + lane;
+            if (e > pos) {
+                d[r] = ud;
+                i[r] = ui;
+            } else if (e == pos) {
+                d[r] = nd;
+                i[r] = ni;
+            }
+        }
+        const int rr = (k - 1) >> 5;
+        float td = d[0];
+        int32_t ti = i[0];
+#pragma unroll
+        for (int r = 1; r < KR; ++r)
+            if (r == rr) {
+                td = d[r];
+                ti = i[r];
+            }
+        thr_d = __shfl_sync(0xffffffffu, td, (k - 1) & 31);
+        thr_i = __shfl_sync(0xffffffffu, ti, (k - 1) & 31);
+    }
+};
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Squared Euclidean distance between the staged query and row `id`.
+__device__ __forceinline__ float row_sq_dist(const float4 *__restrict__ row,
+                                             const float4 *__restrict__ q4, int nv4, int lane) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int j = lane; j < nv4; j += 32) {
+        const float4 x = __ldg(row + j);
+        const float4 q = q4[j];
+        const float dx = q.x - x.x, dy = q.y - x.y, dz = q.z - x.z, dw = q.w - x.w;
+        a0 = __fmaf_rn(dx, dx, a0);
+        a1 = __fmaf_rn(dy, dy, a1);
+        a2 = __fmaf_rn(dz, dz, a2);
+        a3 = __fmaf_rn(dw, dw, a3);
+    }
+    return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+struct VoteSearchArgs {
+    const float *X;
+    int64_t n;
+    int32_t dpad;
+    const float *Q;
+    int64_t m;
+    int32_t d;
+    const int32_t *leaf_of_q;
+    int32_t T_use;
+    const int32_t *leaf_off;
+    const int32_t *leaf_ids;
+    int32_t k, v;
+    int32_t *out_ids;
+    float *out_dists;
+    uint8_t *dbg_votes;
+    int64_t *dbg_ncand;
+    int32_t *dbg_cand;
+    int64_t cand_cap;
+    uint32_t *work;
+};
+
+template <int KR>
+__global__ void __launch_bounds__(VS_THREADS, 1) k_vote_search(const VoteSearchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);                  // CH_WORDS
+    float *qv = reinterpret_cast<float *>(smem + CH_WORDS * 4);            // dpad
+    int32_t *cand = reinterpret_cast<int32_t *>(qv + a.dpad);              // CAND_BUF
+    int32_t *cur = cand + CAND_BUF;                                         // T_use
+    int32_t *lend = cur + a.T_use;                                          // T_use
+    // merge area (aliases the counters once voting is over)
+    float *md = reinterpret_cast<float *>(smem);                            // VS_WARPS * KR*32
+    int32_t *mi = reinterpret_cast<int32_t *>(smem + VS_WARPS * KR * 32 * 4);
+    __shared__ int64_t s_q;
+    __shared__ int s_nc;
+    __shared__ int s_real[VS_WARPS];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nv4 = a.dpad >> 2;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+    const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
+    const int k = a.k;
+    constexpr int K2 = KR * 32;
+
+    for (;;) {
+        if (tid == 0) s_q = int64_t(atomicAdd(a.work, 1u));
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.m) break;
+
+        for (int i = tid; i < a.dpad; i += VS_THREADS) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
+        for (int t = tid; t < a.T_use; t += VS_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * a.T_use + t];
+            cur[t] = a.leaf_off[lf];
+            lend[t] = a.leaf_off[lf + 1];
+        }
+        if (tid == 0) s_nc = 0;
+        WarpTopK<KR> top;
+        top.init();
+        int64_t total = 0;  // |S| so far (uniform)
+
+        for (int64_t c0 = 0; c0 < a.n; c0 += CH_IDS) {
+            const int64_t wleft = (a.n - c0 + 3) >> 2;
+            const int nwords = int(wleft < CH_WORDS ? wleft : int64_t(CH_WORDS));
+            for (int w = tid; w < nwords; w += VS_THREADS) cnt[w] = 0u;
+            __syncthreads();
+            // ---- votes: warp w walks the leaves of trees w, w+16, ...
+            const int64_t lim = c0 + CH_IDS;
+            for (int t = warp; t < a.T_use; t += VS_WARPS) {
+                const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
+                int32_t p = cur[t];
+                const int32_t e = lend[t];
+                while (p < e) {
+                    const int32_t i = p + lane;
+                    const int32_t id = (i < e) ? __ldg(ids + i) : SENTINEL_ID;
+                    const bool ok = int64_t(id) < lim;
+                    if (ok) {
+                        const uint32_t off = uint32_t(int64_t(id) - c0);
+                        atomicAdd(&cnt[off >> 2], 1u << ((off & 3u) * 8u));
+                    }
+                    const int adv = __popc(__ballot_sync(0xffffffffu, ok));
+                    p += adv;
+                    if (adv < 32) break;
+                }
+                if (lane == 0) cur[t] = p;
+            }
+            __syncthreads();
+            // ---- candidates: counters >= v, compacted into `cand`, then
+            // exact distances in batches
+            for (int wb = 0; wb < nwords; wb += VS_THREADS) {
+                const int w = wb + tid;
+                const uint32_t word = (w < nwords) ? cnt[w] : 0u;
+                if (a.dbg_votes != nullptr && w < nwords) {
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t id = c0 + 4 * int64_t(w) + b;
+                        if (id < a.n) a.dbg_votes[qi * a.n + id] = uint8_t((word >> (8 * b)) & 0xffu);
+                    }
+                }
+                uint32_t m4 = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (int((word >> (8 * b)) & 0xffu) >= a.v) m4 |= 1u << b;
+                const int nloc = __popc(m4);
+                int incl = nloc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int base = 0;
+                if (lane == 31 && incl > 0) base = atomicAdd(&s_nc, incl);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                int pos = base + incl - nloc;
+                for (int b = 0; b < 4; ++b)
+                    if (m4 & (1u << b)) cand[pos++] = int32_t(c0 + 4 * int64_t(w) + b);
+                __syncthreads();
+                const int nc = s_nc;
+                const bool last = wb + VS_THREADS >= nwords;
+                if (nc > CAND_BUF - 4 * VS_THREADS || (last && nc > 0)) {
+                    if (a.dbg_cand != nullptr)
+                        for (int i = tid; i < nc; i += VS_THREADS)
+                            if (total + i < a.cand_cap) a.dbg_cand[qi * a.cand_cap + total + i] = cand[i];
+                    int i = warp;
+                    for (; i + VS_WARPS < nc; i += 2 * VS_WARPS) {
+                        const int32_t id0 = cand[i];
+                        const int32_t id1 = cand[i + VS_WARPS];
+                        const float d0 = row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane);
+                        const float d1 = row_sq_dist(X4 + int64_t(id1) * nv4, q4, nv4, lane);
+                        top.insert(d0, id0, k, lane);
+                        top.insert(d1, id1, k, lane);
+                    }
+                    if (i < nc) {
+                        const int32_t id0 = cand[i];
+                        top.insert(row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane), id0, k, lane);
+                    }
+                    total += nc;
+                    __syncthreads();
+                    if (tid == 0) s_nc = 0;
+                    __syncthreads();
+                }
+            }
+        }
+        // ---- merge the warps' lists by rank
+        __syncthreads();
+        {
+            int real = 0;
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int e = r * 32 + lane;
+                md[warp * K2 + e] = top.d[r];
+                mi[warp * K2 + e] = top.i[r];
+                real += (e < k && top.i[r] != SENTINEL_ID) ? 1 : 0;
+            }
+            real = __reduce_add_sync(0xffffffffu, real);
+            if (lane == 0) s_real[warp] = real;
+        }
+        __syncthreads();
+        int all_real = 0;
+        for (int w = 0; w < VS_WARPS; ++w) all_real += s_real[w];
+        const int filled = min(all_real, k);
+        int32_t *oi = a.out_ids + qi * k;
+        float *od = a.out_dists + qi * k;
+        for (int e = filled + tid; e < k; e += VS_THREADS) {
+            oi[e] = -1;
+            od[e] = INFINITY;
+        }
+        for (int x = tid; x < VS_WARPS * k; x += VS_THREADS) {
+            const int w = x / k;
+            const int e = x - w * k;
+            const int32_t id = mi[w * K2 + e];
+            if (id == SENTINEL_ID) continue;
+            const float dd = md[w * K2 + e];
+            int rank = e;
+            for (int w2 = 0; w2 < VS_WARPS && rank < k; ++w2) {
+                if (w2 == w) continue;
+                // entries of list w2 (first k) strictly below (dd, id)
+                int lo = 0, hi = k;
+                const float *ld = md + w2 * K2;
+                const int32_t *li = mi + w2 * K2;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pair_less(ld[mid], li[mid], dd, id))
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                rank += lo;
+            }
+            if (rank < k) {
+                oi[rank] = id;
+                od[rank] = sqrtf(dd);
+            }
+        }
+        if (a.dbg_ncand != nullptr && tid == 0) a.dbg_ncand[qi] = total;
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------- launch ----
+
+namespace {
+
+template <int QT>
+cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    const size_t smem = size_t(QT) * size_t(idx->d) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_query_route<QT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    const dim3 grid(unsigned((ql.m + QT - 1) / QT), unsigned((ql.n_trees + 127) / 128));
+    k_query_route<QT><<<grid, 128, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l, idx->L,
+                                              idx->col_off, idx->dim, idx->val, idx->split,
+                                              ql.leaf, ql.proj, idx->status);
+    return cudaGetLastError();
+}
+
+template <int KR>
+cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    const size_t smem = size_t(CH_WORDS) * 4 + size_t(idx->dpad) * 4 + size_t(CAND_BUF) * 4 +
+                        size_t(2 * ql.n_trees) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_search<KR>, VS_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
+    VoteSearchArgs a;
+    a.X = idx->X;
+    a.n = idx->n;
+    a.dpad = idx->dpad;
+    a.Q = ql.Q;
+    a.m = ql.m;
+    a.d = idx->d;
+    a.leaf_of_q = ql.leaf;
+    a.T_use = ql.n_trees;
+    a.leaf_off = idx->leaf_off;
+    a.leaf_ids = idx->leaf_ids;
+    a.k = ql.k;
+    a.v = ql.v;
+    a.out_ids = ql.out_ids;
+    a.out_dists = ql.out_dists;
+    a.dbg_votes = ql.votes;
+    a.dbg_ncand = ql.n_cand;
+    a.dbg_cand = ql.cand;
+    a.cand_cap = ql.cand_cap;
+    a.work = idx->status + 1;
+    e = cudaMemsetAsync(idx->status + 1, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
+    cudaStream_t s = idx->stream;
+    if (ql.m == 0) return MRPT_OK;
+    const int64_t per_q = int64_t(idx->d) * 4;
+    cudaError_t e;
+    if (per_q * 8 <= 96 * 1024)
+        e = launch_route<8>(idx, ql, s);
+    else if (per_q * 4 <= 96 * 1024)
+        e = launch_route<4>(idx, ql, s);
+    else if (per_q * 2 <= 160 * 1024)
+        e = launch_route<2>(idx, ql, s);
+    else
+        e = launch_route<1>(idx, ql, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    const int kr = (ql.k + 31) / 32;
+    if (kr <= 1)
+        e = launch_vote<1>(idx, ql, s);
+    else if (kr <= 2)
+        e = launch_vote<2>(idx, ql, s);
+    else if (kr <= 4)
+        e = launch_vote<4>(idx, ql, s);
+    else
+        e = launch_vote<8>(idx, ql, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
+    return MRPT_OK;
+}
+
+}  // namespace mrpt

@@ -1,0 +1,88 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/mrpt.h declares; the Python binding mirrors those names.  No
+compute call is made here."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mrpt.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrpt_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1509_06957_gb300 import build
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for name in ("mrpt_build", "mrpt_query", "mrpt_free", "mrpt_last_error"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (mrpt_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_mirrors_abi(lib_path):
+    import paper_1509_06957_gb300 as mr
+    assert set(mr.ABI_SYMBOLS) == set(declared_functions())
+    for name in ("mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
+                 "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export"):
+        assert callable(getattr(mr, name))
+    lib = mr.load_library()
+    assert mr.mrpt_last_error() == ""
+    # argument checks run before any device work, so they work without a GPU
+    h = ctypes.c_void_p()
+    rc = lib.mrpt_build(None, 10, 4, 1, 1, 0.5, 0, ctypes.byref(h))
+    assert rc == mr.MRPT_ERR_INVALID_ARG
+    assert "invalid argument" in mr.mrpt_last_error()
+
+
+def _py_imports(path):
+    import ast
+    tree = ast.parse(open(path).read())
+    mods = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            mods |= {a.name.split(".")[0] for a in node.names}
+        elif isinstance(node, ast.ImportFrom) and node.module and node.level == 0:
+            mods.add(node.module.split(".")[0])
+    return mods
+
+
+def test_oracle_and_library_share_nothing():
+    """The oracle and the CUDA library are independent: neither includes,
+    imports or links the other."""
+    pkg = os.path.join(ROOT, "paper_1509_06957_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                assert "oracle" not in _py_imports(path), path
+            elif f.endswith((".cu", ".cuh", ".h")):
+                incs = re.findall(r'#include\s+[<"]([^>"]+)', open(path).read())
+                assert not any("oracle" in i for i in incs), path
+    assert "paper_1509_06957_gb300" not in _py_imports(os.path.join(ROOT, "oracle", "__init__.py"))
+    otext = open(os.path.join(ROOT, "oracle", "mrpt_oracle.c")).read()
+    assert not any("mrpt.h" in i or "csrc" in i
+                   for i in re.findall(r'#include\s+[<"]([^>"]+)', otext))

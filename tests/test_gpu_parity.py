@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA library (through the C ABI) against the oracle on
+the same seeded inputs.  Bit-exact: random matrix, split values, leaves,
+query projections, leaf of every query, vote counts and candidate sets.
+Distances within 1e-5 relative of the oracle's float64; ids equal except at
+ties."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import REL_TOL, check_index_parity, check_results, oracle_sets
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_06957_gb300 as m
+    m.load_library()
+    return m
+
+
+def _dens(d):
+    return float(np.float32(1.0 / np.sqrt(d)))
+
+
+def _run(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False):
+    dev = torch.device("cuda:0")
+    if host:
+        idx = mr.mrpt_build(X, T, l, density, seed)
+        ids, dists, dbg = mr.mrpt_query_ex(idx, Q, k, v, n_trees=n_trees, debug=True)
+        return idx, ids, dists, dbg
+    idx = mr.mrpt_build(torch.from_numpy(X).to(dev), T, l, density, seed)
+    ids, dists, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).to(dev), k, v, n_trees=n_trees,
+                                       debug=True)
+    torch.cuda.synchronize()
+    return idx, ids.cpu().numpy(), dists.cpu().numpy(), {kk: vv.cpu().numpy() for kk, vv in dbg.items()}
+
+
+def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False):
+    idx, gi, gd, dbg = _run(mr, X, Q, T, l, k, v, density, seed, n_trees, host)
+    ref = oracle.grow_trees(X, T, l, density, seed)
+    check_index_parity(idx, mr, ref)
+    Tq = n_trees or T
+    oi, od, oproj, oleaf, oncand = oracle.query(ref, Q, k, v, T=Tq, want_internals=True)
+    assert np.array_equal(dbg["proj"].view(np.uint32), oproj.view(np.uint32)), "projections"
+    assert np.array_equal(dbg["leaf"], oleaf), "leaf of query"
+    assert np.array_equal(dbg["n_cand"], oncand), "|S|"
+    sets = oracle_sets(ref, oleaf, v, T=Tq)
+    for i in range(len(Q)):
+        F, _ = oracle.votes(ref, oleaf[i], v, T=Tq)
+        assert np.array_equal(dbg["votes"][i], F.astype(np.uint8)), f"votes of query {i}"
+        got = set(dbg["cand"][i][: dbg["n_cand"][i]].tolist())
+        assert got == sets[i], f"candidate set of query {i}"
+    check_results(X, Q, gi, gd, oi, od, sets)
+    idx.close()
+    return gi, gd
+
+
+def test_tiny_gaussian_mixture(mr):
+    """n=10,000, d=128, 100 clusters, T=10, l=6, v=3, k=10, seed 0."""
+    X, Q = workloads.gaussian_mixture(10000, 128, 100, seed=0)
+    _full_check(mr, X, Q, 10, 6, 10, 3, _dens(128), 0)
+
+
+def test_mnist_like_small_with_ties(mr):
+    """Sparse integer images: many projections tie exactly (often at 0), so
+    the (projection, id) median order is exercised."""
+    X, Q = workloads.mnist_like(4000, 40, seed=1)
+    _full_check(mr, X, Q, 16, 5, 10, 2, _dens(784), 3)
+
+
+@pytest.mark.parametrize("k", [1, 33, 100, 256])
+def test_k_values_and_padding(mr, k):
+    X, Q = workloads.gaussian_mixture(1500, 24, 30, n_centres=8, seed=4)
+    _full_check(mr, X, Q, 5, 3, k, 2, 0.3, 5)
+
+
+def test_ragged_dimension_and_host_buffers(mr):
+    """d not a multiple of 4 or 8, n odd, numpy (host) inputs and outputs."""
+    X, Q = workloads.gaussian_mixture(1001, 37, 17, n_centres=6, seed=6)
+    _full_check(mr, X, Q, 7, 4, 10, 2, 0.2, 9, host=True)
+
+
+def test_single_leaf_is_exact_knn(mr):
+    """T = 1, l = 0, v = 1: S = X, so the result is exact k-NN (Sec. I-A)."""
+    X, Q = workloads.gaussian_mixture(700, 19, 20, n_centres=4, seed=8)
+    gi, gd = _full_check(mr, X, Q, 1, 0, 12, 1, 0.5, 1)
+    bi, bd = oracle.brute_knn(X, Q, 12)
+    check_results(X, Q, gi, gd, bi, bd)
+
+
+def test_vote_threshold_equal_to_T_and_subset_of_trees(mr):
+    X, Q = workloads.gaussian_mixture(2500, 32, 25, n_centres=10, seed=9)
+    _full_check(mr, X, Q, 8, 4, 10, 8, _dens(32), 2)
+    _full_check(mr, X, Q, 8, 4, 10, 3, _dens(32), 2, n_trees=5)
+
+
+def test_counter_chunks_beyond_shared_memory(mr):
+    """n > 65,536 ids: votes are counted in id chunks (per-tree cursors)."""
+    X, Q = workloads.gaussian_mixture(140000, 8, 12, n_centres=30, seed=10)
+    _full_check(mr, X, Q, 6, 9, 10, 2, 0.5, 4)
+
+
+def test_degenerate_all_equal_points(mr):
+    """Every projection ties: splits are decided by id alone."""
+    X = np.ones((300, 5), np.float32)
+    Q = np.ones((4, 5), np.float32)
+    _full_check(mr, X, Q, 3, 3, 5, 1, 1.0, 0)
+
+
+def test_empty_batch(mr):
+    X, Q = workloads.gaussian_mixture(200, 8, 1, seed=1)
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 2, 2, 0.5, 0)
+    ids, dists = mr.mrpt_query(idx, torch.empty((0, 8), device="cuda"), 5, 1)
+    assert ids.shape == (0, 5)
+    idx.close()
+
+
+def test_prefix_stable_trees(mr):
+    """The first trees of a larger index are the same trees."""
+    X, _ = workloads.gaussian_mixture(3000, 16, 1, seed=2)
+    a = mr.mrpt_build(X, 4, 5, 0.25, 77)
+    b = mr.mrpt_build(X, 9, 5, 0.25, 77)
+    assert np.array_equal(mr.mrpt_export(a, "SPLIT"), mr.mrpt_export(b, "SPLIT")[:4])
+    assert np.array_equal(mr.mrpt_export(a, "LEAF_IDS"), mr.mrpt_export(b, "LEAF_IDS")[:4])
+    a.close()
+    b.close()
+
+
+@pytest.mark.slow
+def test_mnist_like_full_size_sampled(mr):
+    """n=60,000, d=784, l=8 (the benchmark's shape) at T=50: full index
+    parity, and a sample of 64 queries through every internal."""
+    X, Q = workloads.mnist_like(60000, 64, seed=0)
+    _full_check(mr, X, Q, 50, 8, 10, 4, _dens(784), 0)
+
+
+# ---------------------------------------------------------------- errors --
+
+def test_invalid_arguments(mr):
+    X = np.zeros((16, 4), np.float32)
+    for args in [(X, 0, 1), (X, 256, 1), (X, 2, 5), (X, 2, -1)]:
+        with pytest.raises(mr.MRPTError) as e:
+            mr.mrpt_build(*args)
+        assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+    idx = mr.mrpt_build(X + np.arange(16, dtype=np.float32)[:, None], 2, 2, 1.0, 0)
+    q = np.zeros((2, 4), np.float32)
+    for k, v in [(0, 1), (257, 1), (3, 0), (3, 3)]:
+        with pytest.raises(mr.MRPTError) as e:
+            mr.mrpt_query(idx, q, k, v)
+        assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+    idx.close()
+
+
+def test_nonfinite_inputs(mr):
+    X = np.random.default_rng(0).standard_normal((64, 6)).astype(np.float32)
+    bad = X.copy()
+    bad[5, 2] = np.nan
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_build(bad, 2, 2, 0.5, 0)
+    assert e.value.code == mr.MRPT_ERR_NONFINITE_INPUT
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 2, 2, 0.5, 0)
+    q = torch.zeros((3, 6), device="cuda")
+    q[1, 3] = float("inf")
+    mr.mrpt_query(idx, q, 4, 1)  # device buffers: latched, reported by sync
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_sync(idx)
+    assert e.value.code == mr.MRPT_ERR_NONFINITE_INPUT
+    mr.mrpt_sync(idx)  # cleared
+    with pytest.raises(mr.MRPTError) as e:  # host buffers: reported by the call
+        mr.mrpt_query(idx, q.cpu().numpy(), 4, 1)
+    assert e.value.code == mr.MRPT_ERR_NONFINITE_INPUT
+    idx.close()
+
+
+def test_injected_allocation_failure(mr):
+    X = np.random.default_rng(1).standard_normal((128, 8)).astype(np.float32)
+    for after in range(0, 6):
+        mr.mrpt_debug_fail_alloc_after(after)
+        try:
+            idx = mr.mrpt_build(X, 3, 3, 0.5, 0)
+            idx.close()
+        except mr.MRPTError as e:
+            assert e.code == mr.MRPT_ERR_OOM
+        finally:
+            mr.mrpt_debug_fail_alloc_after(-1)
+    idx = mr.mrpt_build(X, 3, 3, 0.5, 0)  # the library is still usable
+    ids, _ = mr.mrpt_query(idx, X[:4], 3, 1)
+    assert ids[:, 0].tolist() == [0, 1, 2, 3]
+    idx.close()
