@@ -1,0 +1,458 @@
+"""Benchmark: query throughput of MRPT with voting on one GB300.
+
+Workload (default): 60,000 x 784 stroke images with integer pixel values
+0..255 and about 80 % zeros (the MNIST shape of Table II), 10,000 held-out
+queries, k = 10, trees of depth 8.  The number of trees T (50/100/200, taken
+as prefixes of one 200-tree index) and the vote threshold v (1..10) are
+picked by a sweep: the fastest (T, v) whose recall@10 reaches 0.9.  A step
+is one query pass over the 10,000 queries (projection, routing, voting,
+candidate distances, top-k), inputs resident in HBM; L2 is flushed before
+every timed step.
+
+Prints one JSON line (see the keys below).  ``--impl reference`` times the
+CPU oracle instead, on a bounded sample of the same workload.
+Multi-GPU (torchrun, N > 1): every rank holds a replica of the index and
+answers its own 10,000 queries (weak scaling; no collective on the path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = dict(name="mnist-like 60000x784 u8-valued fp32, 10000 queries, k=10, depth 8",
+                n=60000, d=784, m=10000, k=10, l=8, T_max=200, T_grid=(50, 100, 200),
+                v_grid=tuple(range(1, 11)), seed=0, target_recall=0.9)
+METRIC = "queries/sec at recall@10>=0.9 (mnist-like 60000x784, k=10)"
+
+
+# ----------------------------------------------------------------- utils --
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_range(m: int, world: int, rank: int):
+    """Queries [lo, hi) of rank `rank` when m queries are split evenly."""
+    base, extra = divmod(m, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "vote_search_mnist60k.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    if j.get("source_sha") != source_sha(kernel_src):
+        return None
+    return j.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------- ground truth -----
+
+def exact_knn_gpu(X, Q, k, torch):
+    """Exact k-NN in float64 on the GPU (ground truth for recall only).
+    Returns (ids, kth distance^2) with ids ordered by (distance, id)."""
+    Xd = X.double()
+    xn = (Xd * Xd).sum(1)
+    ids_out, kth_out = [], []
+    for s in range(0, Q.shape[0], 512):
+        q = Q[s:s + 512].double()
+        d2 = (q * q).sum(1, keepdim=True) + xn[None, :] - 2.0 * (q @ Xd.T)
+        vals, idx = torch.topk(d2, k + 8, dim=1, largest=False, sorted=True)
+        # order by (distance, id) among the k + 8 smallest
+        key = torch.argsort(idx, dim=1)
+        vals, idx = torch.gather(vals, 1, key), torch.gather(idx, 1, key)
+        key = torch.argsort(vals, dim=1, stable=True)
+        vals, idx = torch.gather(vals, 1, key), torch.gather(idx, 1, key)
+        ids_out.append(idx[:, :k])
+        kth_out.append(vals[:, k - 1])
+    return torch.cat(ids_out), torch.cat(kth_out)
+
+
+def recall_at_k(ids, X, Q, gt_ids, gt_kth, torch):
+    """Recall |A n K| / k (Sec. I-A): strict (K ordered by (distance, id))
+    and tie-aware (a returned point counts when its exact distance is at
+    most the true k-th distance)."""
+    m, k = gt_ids.shape
+    strict = 0
+    for s in range(0, m, 2048):
+        a = ids[s:s + 2048].long()
+        g = gt_ids[s:s + 2048].long()
+        strict += (a[:, :, None] == g[:, None, :]).any(2).sum().item()
+    valid = ids >= 0
+    a = ids.clamp(min=0).long()
+    ta = 0
+    for s in range(0, m, 1024):
+        rows = X[a[s:s + 1024]].double()                       # b x k x d
+        q = Q[s:s + 1024].double()[:, None, :]
+        d2 = ((rows - q) ** 2).sum(2)
+        ok = (d2 <= gt_kth[s:s + 1024, None] * (1 + 1e-12)) & valid[s:s + 1024]
+        ta += ok.sum().item()
+    return strict / (m * k), ta / (m * k)
+
+
+# ------------------------------------------------------------- GPU arm ----
+
+def run_gpu(args):
+    import torch
+    import paper_1509_06957_gb300 as mr
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = WORKLOAD
+    X_np, Q_np = workloads.mnist_like(W["n"], W["m"], seed=W["seed"])
+    X = torch.from_numpy(X_np).to(dev)
+    Q = torch.from_numpy(Q_np).to(dev)
+    n, d, m, k, l = W["n"], W["d"], W["m"], W["k"], W["l"]
+
+    # ---- build (timed once)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    index = mr.mrpt_build(X, W["T_max"], l, 0.0, seed=W["seed"])
+    build_s = time.perf_counter() - t0
+
+    gt_ids, gt_kth = exact_knn_gpu(X, Q, k, torch)
+    ids = torch.empty((m, k), dtype=torch.int32, device=dev)
+    dists = torch.empty((m, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def query(T_use, v, stage=None):
+        mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, out_ids=ids, out_dists=dists,
+                         stage_ms=stage)
+
+    # ---- sweep (T, v): fastest with recall >= target (tie-aware), unless
+    # the operating point is given
+    sweep = []
+    stage = np.zeros(3, np.float32)
+    grid = [(args.T, args.v)] if args.T and args.v else \
+        [(T_, v_) for T_ in W["T_grid"] for v_ in W["v_grid"] if v_ <= T_]
+    for T_use, v in grid:
+        query(T_use, v)  # warm
+        flush.zero_()
+        query(T_use, v, stage)
+        rs, rt = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
+        sweep.append(dict(T=T_use, v=v, ms=float(stage[2]), recall=round(rt, 4),
+                          recall_strict=round(rs, 4)))
+    ok = [s for s in sweep if s["recall"] >= W["target_recall"]]
+    best = min(ok, key=lambda s: s["ms"]) if ok else max(sweep, key=lambda s: s["recall"])
+    T_use, v = best["T"], best["v"]
+
+    # ---- mean |S| at the operating point (untimed debug pass)
+    _, _, dbg = mr.mrpt_query_ex(index, Q[:2000], k, v, n_trees=T_use, debug=True, cand_cap=1)
+    mean_S = float(dbg["n_cand"].double().mean().item())
+    del dbg
+
+    # ---- timed steps (device-resident inputs)
+    for _ in range(args.warmup):
+        query(T_use, v)
+    torch.cuda.synchronize()
+    per_step, vote_ms, route_ms = [], [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            query(T_use, v, stage)
+            route_ms.append(float(stage[0]))
+            vote_ms.append(float(stage[1]))
+            per_step.append(float(stage[2]))
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.summary()
+    total_ms = sum(per_step)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * m * args.steps / (total_ms / 1e3)
+    recall_strict, recall_ta = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch)
+
+    # ---- roofline of the dominant kernel (vote/search)
+    peak, peak_kind = load_peaks()
+    L = 1 << l
+    leaf_bytes = T_use * math.ceil(n / L) * 4
+    cand_bytes = mean_S * d * 4
+    per_query = leaf_bytes + cand_bytes + d * 4 + T_use * 4 + k * 8
+    vote_avg_ms = statistics.mean(vote_ms)
+    achieved = per_query * m / (vote_avg_ms / 1e3) / 1e9
+    kernel_src = [os.path.join(ROOT, "paper_1509_06957_gb300", "csrc", "mrpt_query.cu")]
+    traffic = load_traffic(kernel_src)
+    dedup = (leaf_bytes + d * 4 + T_use * 4 + k * 8) * m + min(n, mean_S * m) * d * 4
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} hbm_gbs",
+                "kernel": "k_vote_search",
+                "algorithmic_bytes_per_query": round(per_query, 1),
+                "frac_dedup_rows": round(dedup / (vote_avg_ms / 1e3) / 1e9 / peak, 4)}
+
+    out = None
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline(X_np, Q_np, T_use, v, k, l)
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W["name"], "n": n, "d": d, "queries_per_step": m, "k": k,
+                       "depth": l, "T": T_use, "v": v, "density": "1/sqrt(d)",
+                       "recall_at_10": round(recall_ta, 4),
+                       "recall_at_10_strict": round(recall_strict, 4),
+                       "mean_candidates": round(mean_S, 1), "build_s_T200": round(build_s, 3),
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "stage_ms": {"route": round(statistics.mean(route_ms), 4),
+                         "vote_search": round(vote_avg_ms, 4)},
+            "sweep": sweep,
+        }
+        print(json.dumps(out), flush=True)
+    index.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch):
+    """The same metric through the public call with pinned host buffers:
+    every step copies the queries in and the results out."""
+    m, d = Q.shape
+    Qh = Q.cpu().pin_memory().numpy()
+    ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory().numpy()
+    dists_h = torch.empty((m, k), dtype=torch.float32).pin_memory().numpy()
+    mr.mrpt_query(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h)
+    el = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mr.mrpt_query(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h)
+        el += time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el], device=Q.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    return {"value": round(world * m * args.steps / el, 1), "unit": "queries/s",
+            "h2d_bytes_per_step": int(m * d * 4), "d2h_bytes_per_step": int(m * k * 8)}
+
+
+# ------------------------------------------------------- CPU (oracle) -----
+
+def _oracle_index(X, T, l, seed):
+    """The oracle's own index (Algorithm 1), trees grown on a thread pool."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    d = X.shape[1]
+    dens = float(np.float32(1.0 / np.sqrt(d)))
+    R = oracle.random_matrix(T, l, d, dens, seed)
+    P = oracle.project_threads(X, R) if hasattr(oracle, "project_threads") else oracle.project(X, R)
+    L = 1 << l
+    split = np.zeros((T, L - 1), np.float32)
+    leaf_off = np.zeros((T, L + 1), np.int32)
+    leaf_ids = np.zeros((T, X.shape[0]), np.int32)
+
+    def one(t):
+        s, o, i = oracle.grow_tree(P, t * l, l)
+        split[t], leaf_off[t], leaf_ids[t] = s, o, i
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        list(ex.map(one, range(T)))
+    return oracle.Index(X, T, l, R, P, split, leaf_off, leaf_ids)
+
+
+def cpu_baseline(X, Q, T, v, k, l, target_s=15.0):
+    """The oracle's query path (float32 distances) on all host cores, on a
+    bounded sample of the queries."""
+    import oracle
+    ref = _oracle_index(X, T, l, WORKLOAD["seed"])
+    threads = oracle.max_threads()
+    probe = Q[: max(threads, 8)]
+    t0 = time.perf_counter()
+    oracle.query(ref, probe, k, v, mode=1, nthreads=threads)
+    per_q = (time.perf_counter() - t0) / len(probe)
+    ns = int(min(len(Q), max(len(probe), target_s / max(per_q, 1e-6))))
+    sample = Q[:ns]
+    t0 = time.perf_counter()
+    oracle.query(ref, sample, k, v, mode=1, nthreads=threads)
+    el = time.perf_counter() - t0
+    return {"value": round(ns / el, 2), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {ns} of the {len(Q)} queries, T={T}, v={v}, float32 distances, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same workload, metric and
+    operating point, each step a bounded sample of the queries."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    W = WORKLOAD
+    X, Q = workloads.mnist_like(W["n"], W["m"], seed=W["seed"])
+    T, v = args.ref_T, args.ref_v
+    ref = _oracle_index(X, T, W["l"], W["seed"])
+    threads = oracle.max_threads()
+    probe = Q[:threads]
+    t0 = time.perf_counter()
+    oracle.query(ref, probe, W["k"], v, mode=1, nthreads=threads)
+    per_q = (time.perf_counter() - t0) / len(probe)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    ns = int(min(len(Q), max(threads, budget / max(per_q, 1e-6))))
+    for i in range(args.warmup):
+        oracle.query(ref, Q[:ns], W["k"], v, mode=1, nthreads=threads)
+    el = 0.0
+    for i in range(args.steps):
+        s = (i * ns) % len(Q)
+        sample = np.ascontiguousarray(np.roll(Q, -s, axis=0)[:ns])
+        t0 = time.perf_counter()
+        oracle.query(ref, sample, W["k"], v, mode=1, nthreads=threads)
+        el += time.perf_counter() - t0
+    qps = ns * args.steps / el
+    out = {"metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": W["name"], "n": W["n"], "d": W["d"], "k": W["k"],
+                      "depth": W["l"], "T": T, "v": v, "queries_per_step": ns},
+           "cpu_baseline": {"value": round(qps, 2), "unit": "queries/s", "cores": threads,
+                            "kind": "oracle",
+                            "sample": f"{ns} queries per step of the {len(Q)}"},
+           "e2e": {"value": round(qps, 2), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--T", type=int, default=0, help="fix the number of trees (with --v)")
+    ap.add_argument("--v", type=int, default=0, help="fix the vote threshold (with --T)")
+    ap.add_argument("--ref-T", type=int, default=100)
+    ap.add_argument("--ref-v", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

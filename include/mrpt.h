@@ -113,6 +113,10 @@ typedef struct mrpt_query_opts {
     int64_t *n_cand;      /* m: |S| */
     int32_t *cand;        /* m x cand_cap: members of S (any order) */
     int64_t cand_cap;     /* row capacity of `cand`; members past it are dropped */
+    /* host float[3] (NULL = not measured): device time in ms of the routing
+     * kernel, of the vote/search kernel and of the whole query, from CUDA
+     * events recorded on the index's stream; the call then synchronises */
+    float *stage_ms;
 } mrpt_query_opts;
 
 int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,

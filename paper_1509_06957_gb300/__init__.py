@@ -70,6 +70,7 @@ class QueryOpts(ctypes.Structure):
         ("n_cand", ctypes.c_void_p),
         ("cand", ctypes.c_void_p),
         ("cand_cap", ctypes.c_int64),
+        ("stage_ms", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -266,11 +267,14 @@ def mrpt_info(index: Index) -> IndexInfo:
 
 
 def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
-                  out_dists=None, debug: bool = False, cand_cap: int | None = None):
+                  out_dists=None, debug: bool = False, cand_cap: int | None = None,
+                  stage_ms=None):
     """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
     tensors for a CUDA tensor, numpy arrays for host input) unless given.
     With ``debug`` also returns a dict of the internals: proj, leaf, votes,
-    n_cand and cand (members of S, row padded)."""
+    n_cand and cand (members of S, row padded).  ``stage_ms`` (a float32
+    numpy array of 3) receives the routing, vote/search and total device
+    times of this call in ms."""
     lib = load_library()
     Q = _as_f32(Q)
     m = Q.shape[0]
@@ -283,6 +287,9 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
         _check(lib.mrpt_set_stream(index.handle, stream))
     opts = QueryOpts()
     opts.n_trees = int(n_trees)
+    if stage_ms is not None:
+        assert stage_ms.dtype == np.float32 and stage_ms.size >= 3
+        opts.stage_ms = stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     dbg = None
     if debug:
         T_use = n_trees if n_trees > 0 else index.T

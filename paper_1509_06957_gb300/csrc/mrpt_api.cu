@@ -87,6 +87,8 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->leaf_off);
     cudaFree(idx->leaf_ids);
     cudaFree(idx->status);
+    for (cudaEvent_t &ev : idx->ev)
+        if (ev) cudaEventDestroy(ev);
     idx->q_leaf.release();
     idx->q_stage.release();
     idx->o_stage.release();
@@ -350,6 +352,7 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         ql.n_cand = static_cast<int64_t *>(dev_of(3));
         ql.cand = static_cast<int32_t *>(dev_of(4));
         ql.cand_cap = opts->cand_cap;
+        ql.stage_ms = opts->stage_ms;
     }
     if (!ql.leaf) {
         if ((rc = idx->q_leaf.ensure(leaf_b, "leaf-of-query scratch"))) return rc;

@@ -79,6 +79,7 @@ struct mrpt_index {
     mrpt::Scratch dbg_stage; // staged debug outputs
 
     int64_t device_bytes = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // stage timing (created on first use)
 };
 
 namespace mrpt {
@@ -113,6 +114,7 @@ struct QueryLaunch {
     int64_t *n_cand;       // optional m
     int32_t *cand;         // optional m x cand_cap
     int64_t cand_cap;
+    float *stage_ms;       // optional host float[3]
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);

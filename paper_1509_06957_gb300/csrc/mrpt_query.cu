@@ -438,6 +438,11 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     if (ql.m == 0) return MRPT_OK;
     const int64_t per_q = int64_t(idx->d) * 4;
     cudaError_t e;
+    if (ql.stage_ms) {
+        for (int i = 0; i < 3; ++i)
+            if (!idx->ev[i]) MRPT_CUDA_TRY(cudaEventCreate(&idx->ev[i]));
+        MRPT_CUDA_TRY(cudaEventRecord(idx->ev[0], s));
+    }
     if (per_q * 8 <= 96 * 1024)
         e = launch_route<8>(idx, ql, s);
     else if (per_q * 4 <= 96 * 1024)
@@ -447,6 +452,7 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     else
         e = launch_route<1>(idx, ql, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[1], s));
     const int kr = (ql.k + 31) / 32;
     if (kr <= 1)
         e = launch_vote<1>(idx, ql, s);
@@ -457,6 +463,13 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     else
         e = launch_vote<8>(idx, ql, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
+    if (ql.stage_ms) {
+        MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
+        MRPT_CUDA_TRY(cudaEventSynchronize(idx->ev[2]));
+        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[0], idx->ev[0], idx->ev[1]));
+        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[1], idx->ev[1], idx->ev[2]));
+        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[2], idx->ev[0], idx->ev[2]));
+    }
     return MRPT_OK;
 }
 
