@@ -79,11 +79,10 @@ __global__ void __launch_bounds__(128) k_query_route(
 
 // ---------------------------------------------------------- vote search ----
 
-constexpr int VS_THREADS = 512;
+constexpr int VS_THREADS = 256;
 constexpr int VS_WARPS = VS_THREADS / 32;
 constexpr int CH_WORDS = 16384;          // 64 KB: 8-bit counters for 65,536 ids
 constexpr int64_t CH_IDS = int64_t(CH_WORDS) * 4;
-constexpr int CAND_BUF = 4096;           // candidate ids buffered per batch
 constexpr int32_t SENTINEL_ID = 0x7fffffff;
 
 __device__ __forceinline__ bool pair_less(float da, int32_t ia, float db, int32_t ib) {
@@ -194,34 +193,59 @@ struct VoteSearchArgs {
     int32_t *dbg_cand;
     int64_t cand_cap;
     uint32_t *work;
+    int32_t cnt_words;     // counter words per chunk (<= CH_WORDS, multiple of 4)
+    int32_t region_bytes;  // bytes of the counter / merge region (multiple of 16)
 };
 
+// Per warp: a buffer of emitted candidates waiting for their distances.
+constexpr int WBUF = 256;
+
+// One block per query at a time (queries taken from an atomic counter).
+//   1. clear the 8-bit vote counters of the id chunk [c0, c0 + CH_IDS);
+//   2. every warp walks the leaves of its trees (t = warp, warp + W, ...),
+//      128 ids per step, and adds one vote per id with a shared-memory
+//      atomic; the lane whose increment takes a count from v-1 to v emits
+//      the id (Algorithm 4: "if votes[point] = v then S <- S u {point}");
+//   3. a warp computes the exact distances of the ids it emitted itself
+//      (64 or more at a time) and keeps them in its own top-k -- warps
+//      never wait for each other between the clear and the merge;
+//   4. the warps' top-k lists are merged by rank.
+// Emission is final (votes only grow), so a candidate's distance can be
+// computed as soon as it is emitted.  Ids above the chunk are left for the
+// next chunk through per-tree cursors (leaves list ids in ascending order).
 template <int KR>
-__global__ void __launch_bounds__(VS_THREADS, 1) k_vote_search(const VoteSearchArgs a) {
+__global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);                  // CH_WORDS
-    float *qv = reinterpret_cast<float *>(smem + CH_WORDS * 4);            // dpad
-    int32_t *cand = reinterpret_cast<int32_t *>(qv + a.dpad);              // CAND_BUF
-    int32_t *cur = cand + CAND_BUF;                                         // T_use
-    int32_t *lend = cur + a.T_use;                                          // T_use
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);                        // a.cnt_words
+    float *qv = reinterpret_cast<float *>(smem + size_t(a.region_bytes));      // dpad
+    int32_t *wbuf = reinterpret_cast<int32_t *>(qv + a.dpad);                  // VS_WARPS * WBUF
+    int32_t *cur = wbuf + VS_WARPS * WBUF;                                      // T_use
+    int32_t *lend = cur + a.T_use;                                              // T_use
     // merge area (aliases the counters once voting is over)
-    float *md = reinterpret_cast<float *>(smem);                            // VS_WARPS * KR*32
+    float *md = reinterpret_cast<float *>(smem);                                // VS_WARPS * KR*32
     int32_t *mi = reinterpret_cast<int32_t *>(smem + VS_WARPS * KR * 32 * 4);
     __shared__ int64_t s_q;
-    __shared__ int s_nc;
+    __shared__ unsigned long long s_total;
     __shared__ int s_real[VS_WARPS];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int nv4 = a.dpad >> 2;
     const float4 *q4 = reinterpret_cast<const float4 *>(qv);
     const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
     const int k = a.k;
+    const uint32_t vm1 = uint32_t(a.v - 1);
+    const bool track = (a.dbg_ncand != nullptr) || (a.dbg_cand != nullptr);
     constexpr int K2 = KR * 32;
+    int32_t *mybuf = wbuf + warp * WBUF;
 
     for (;;) {
-        if (tid == 0) s_q = int64_t(atomicAdd(a.work, 1u));
+        if (tid == 0) {
+            s_q = int64_t(atomicAdd(a.work, 1u));
+            s_total = 0ull;
+        }
         __syncthreads();
         const int64_t qi = s_q;
         if (qi >= a.m) break;
@@ -232,94 +256,100 @@ __global__ void __launch_bounds__(VS_THREADS, 1) k_vote_search(const VoteSearchA
             cur[t] = a.leaf_off[lf];
             lend[t] = a.leaf_off[lf + 1];
         }
-        if (tid == 0) s_nc = 0;
         WarpTopK<KR> top;
         top.init();
-        int64_t total = 0;  // |S| so far (uniform)
+
+        // exact distances of this warp's buffered candidates
+        auto drain = [&](int nb) {
+            __syncwarp();
+            int j = 0;
+            for (; j + 1 < nb; j += 2) {
+                const int32_t id0 = mybuf[j];
+                const int32_t id1 = mybuf[j + 1];
+                const float d0 = row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane);
+                const float d1 = row_sq_dist(X4 + int64_t(id1) * nv4, q4, nv4, lane);
+                top.insert(d0, id0, k, lane);
+                top.insert(d1, id1, k, lane);
+            }
+            if (j < nb) {
+                const int32_t id0 = mybuf[j];
+                top.insert(row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane), id0, k, lane);
+            }
+            __syncwarp();
+        };
 
         for (int64_t c0 = 0; c0 < a.n; c0 += CH_IDS) {
             const int64_t wleft = (a.n - c0 + 3) >> 2;
-            const int nwords = int(wleft < CH_WORDS ? wleft : int64_t(CH_WORDS));
-            for (int w = tid; w < nwords; w += VS_THREADS) cnt[w] = 0u;
+            const int nwords = int(wleft < a.cnt_words ? wleft : int64_t(a.cnt_words));
+            {
+                uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+                const int n4 = (nwords + 3) >> 2;
+                for (int w = tid; w < n4; w += VS_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
+            }
             __syncthreads();
-            // ---- votes: warp w walks the leaves of trees w, w+16, ...
             const int64_t lim = c0 + CH_IDS;
+            int nb = 0;
             for (int t = warp; t < a.T_use; t += VS_WARPS) {
                 const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
                 int32_t p = cur[t];
                 const int32_t e = lend[t];
                 while (p < e) {
-                    const int32_t i = p + lane;
-                    const int32_t id = (i < e) ? __ldg(ids + i) : SENTINEL_ID;
-                    const bool ok = int64_t(id) < lim;
-                    if (ok) {
-                        const uint32_t off = uint32_t(int64_t(id) - c0);
-                        atomicAdd(&cnt[off >> 2], 1u << ((off & 3u) * 8u));
+                    int32_t id[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t i = p + 32 * u + lane;
+                        id[u] = (i < e) ? __ldg(ids + i) : SENTINEL_ID;
                     }
-                    const int adv = __popc(__ballot_sync(0xffffffffu, ok));
+                    int adv = 0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool ok = int64_t(id[u]) < lim;
+                        bool emit = false;
+                        if (ok) {
+                            const uint32_t off = uint32_t(int64_t(id[u]) - c0);
+                            const uint32_t sh = (off & 3u) * 8u;
+                            const uint32_t old = atomicAdd(&cnt[off >> 2], 1u << sh);
+                            emit = ((old >> sh) & 0xffu) == vm1;
+                        }
+                        adv += __popc(__ballot_sync(0xffffffffu, ok));
+                        const unsigned em = __ballot_sync(0xffffffffu, emit);
+                        if (em) {
+                            if (emit) mybuf[nb + __popc(em & lt)] = id[u];
+                            if (track) {
+                                unsigned long long base = 0;
+                                if (lane == 0) base = atomicAdd(&s_total, (unsigned long long)__popc(em));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (emit && a.dbg_cand != nullptr) {
+                                    const int64_t slot = int64_t(base) + __popc(em & lt);
+                                    if (slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                                }
+                            }
+                            nb += __popc(em);
+                        }
+                    }
+                    if (nb >= 64) {
+                        drain(nb);
+                        nb = 0;
+                    }
                     p += adv;
-                    if (adv < 32) break;
+                    if (adv < 128) break;
                 }
                 if (lane == 0) cur[t] = p;
             }
+            if (nb > 0) drain(nb);
             __syncthreads();
-            // ---- candidates: counters >= v, compacted into `cand`, then
-            // exact distances in batches
-            for (int wb = 0; wb < nwords; wb += VS_THREADS) {
-                const int w = wb + tid;
-                const uint32_t word = (w < nwords) ? cnt[w] : 0u;
-                if (a.dbg_votes != nullptr && w < nwords) {
+            if (a.dbg_votes != nullptr) {
+                for (int w = tid; w < nwords; w += VS_THREADS) {
+                    const uint32_t word = cnt[w];
                     for (int b = 0; b < 4; ++b) {
                         const int64_t id = c0 + 4 * int64_t(w) + b;
                         if (id < a.n) a.dbg_votes[qi * a.n + id] = uint8_t((word >> (8 * b)) & 0xffu);
                     }
                 }
-                uint32_t m4 = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (int((word >> (8 * b)) & 0xffu) >= a.v) m4 |= 1u << b;
-                const int nloc = __popc(m4);
-                int incl = nloc;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                int base = 0;
-                if (lane == 31 && incl > 0) base = atomicAdd(&s_nc, incl);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                int pos = base + incl - nloc;
-                for (int b = 0; b < 4; ++b)
-                    if (m4 & (1u << b)) cand[pos++] = int32_t(c0 + 4 * int64_t(w) + b);
                 __syncthreads();
-                const int nc = s_nc;
-                const bool last = wb + VS_THREADS >= nwords;
-                if (nc > CAND_BUF - 4 * VS_THREADS || (last && nc > 0)) {
-                    if (a.dbg_cand != nullptr)
-                        for (int i = tid; i < nc; i += VS_THREADS)
-                            if (total + i < a.cand_cap) a.dbg_cand[qi * a.cand_cap + total + i] = cand[i];
-                    int i = warp;
-                    for (; i + VS_WARPS < nc; i += 2 * VS_WARPS) {
-                        const int32_t id0 = cand[i];
-                        const int32_t id1 = cand[i + VS_WARPS];
-                        const float d0 = row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane);
-                        const float d1 = row_sq_dist(X4 + int64_t(id1) * nv4, q4, nv4, lane);
-                        top.insert(d0, id0, k, lane);
-                        top.insert(d1, id1, k, lane);
-                    }
-                    if (i < nc) {
-                        const int32_t id0 = cand[i];
-                        top.insert(row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane), id0, k, lane);
-                    }
-                    total += nc;
-                    __syncthreads();
-                    if (tid == 0) s_nc = 0;
-                    __syncthreads();
-                }
             }
         }
         // ---- merge the warps' lists by rank
-        __syncthreads();
         {
             int real = 0;
 #pragma unroll
@@ -369,7 +399,7 @@ __global__ void __launch_bounds__(VS_THREADS, 1) k_vote_search(const VoteSearchA
                 od[rank] = sqrtf(dd);
             }
         }
-        if (a.dbg_ncand != nullptr && tid == 0) a.dbg_ncand[qi] = total;
+        if (a.dbg_ncand != nullptr && tid == 0) a.dbg_ncand[qi] = int64_t(s_total);
         __syncthreads();
     }
 }
@@ -393,7 +423,14 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
 
 template <int KR>
 cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const size_t smem = size_t(CH_WORDS) * 4 + size_t(idx->dpad) * 4 + size_t(CAND_BUF) * 4 +
+    // counters for min(n, CH_IDS) ids, rounded to 16 bytes; the same region
+    // later holds the warps' top-k lists for the merge
+    const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
+    const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
+    const size_t merge_bytes = size_t(VS_WARPS) * KR * 32 * 8;
+    size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
+    region = (region + 15) & ~size_t(15);
+    const size_t smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 +
                         size_t(2 * ql.n_trees) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -425,6 +462,8 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     a.dbg_cand = ql.cand;
     a.cand_cap = ql.cand_cap;
     a.work = idx->status + 1;
+    a.cnt_words = cnt_words;
+    a.region_bytes = int(region);
     e = cudaMemsetAsync(idx->status + 1, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
