@@ -1,9 +1,9 @@
 // Query phase (Sec. III, Algorithms 3-4) on sm_103a.
 //
-//   k_query_route   p = q^T R for every tree and level (Algorithm 3, line
-//                   "p <- q^T R"), then the descent p[level] <= split -> left.
-//                   A block stages a tile of queries in shared memory; one
-//                   thread owns one tree for every query of the tile.
+//   k_query_route   p = q^T R for every tree and level (Algorithm 3), then
+//                   the descent p[level] <= split -> left.  A block stages up
+//                   to 32 queries in shared memory; one thread per (query,
+//                   tree), lanes of a warp share trees.
 //   k_vote_search   persistent blocks take queries from an atomic counter.
 //                   Per query: 8-bit vote counters for a chunk of point ids
 //                   in shared memory, incremented by warp-wide passes over
@@ -25,56 +25,110 @@ namespace mrpt {
 
 // ------------------------------------------------------------- routing ----
 
-template <int QT>
-__global__ void __launch_bounds__(128) k_query_route(
+// One thread per (query, tree): lane = query (QB = 32 queries per tile, or
+// QB < 32 queries x 32/QB trees per warp when d is large).  Work items are
+// (query tile, group of ROUTE_TREES_PER_ITEM trees); a persistent block
+// takes a contiguous range of items, so it stages a query tile once and
+// walks its tree groups.  All lanes that share a tree read the same
+// nonzero (dim, val) -- a broadcast load -- and take their query's
+// component from shared memory (odd row stride: no bank conflicts).  Each
+// projection is an fmaf chain in ascending dimension from +0.0f, followed by
+// the descent p <= split -> left (Algorithm 3).
+constexpr int ROUTE_TREES_PER_ITEM = 16;
+
+template <int QB>
+__global__ void __launch_bounds__(512) k_query_route(
     const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
     const int32_t *__restrict__ col_off, const int32_t *__restrict__ dim,
     const float *__restrict__ val, const float *__restrict__ split, int32_t *__restrict__ leaf,
-    float *__restrict__ proj, uint32_t *__restrict__ status) {
-    extern __shared__ float qs[];  // QT x d
-    const int64_t q0 = int64_t(blockIdx.x) * QT;
-    const int nq = int((m - q0) < QT ? (m - q0) : int64_t(QT));
-    bool bad = false;
-    for (int i = threadIdx.x; i < QT * d; i += blockDim.x) {
-        const int r = i / d;
-        float x = 0.f;
-        if (r < nq) {
-            x = Q[q0 * d + i];
-            bad |= !isfinite(x);
-        }
-        qs[i] = x;
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, STATUS_NONFINITE_QUERY);
-    __syncthreads();
-    const int t = blockIdx.y * blockDim.x + threadIdx.x;
-    if (t >= T_use) return;
+    float *__restrict__ proj, uint32_t *__restrict__ status, int64_t n_items) {
+    extern __shared__ float qs[];  // QB x (d | 1)
+    const int stride = d | 1;
+    constexpr int G = 32 / QB;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int qq = lane % QB;
+    const int g = lane / QB;
+    const float *qrow = qs + qq * stride;
     const int64_t inner = L - 1;
-    const float *sp = split + int64_t(t) * inner;
-    int32_t node[QT];
-#pragma unroll
-    for (int q = 0; q < QT; ++q) node[q] = 0;
     const int ncols = T_use * l;
-    for (int j = 0; j < l; ++j) {
-        const int c = t * l + j;
-        float acc[QT];
-#pragma unroll
-        for (int q = 0; q < QT; ++q) acc[q] = 0.0f;
-        const int e1 = col_off[c + 1];
-        for (int e = col_off[c]; e < e1; ++e) {
-            const int dd = dim[e];
-            const float vv = val[e];
-#pragma unroll
-            for (int q = 0; q < QT; ++q) acc[q] = __fmaf_rn(qs[q * d + dd], vv, acc[q]);
+    const int groups = (T_use + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM;
+    const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
+    // contiguous item range of this block
+    const int64_t per = n_items / gridDim.x, extra = n_items % gridDim.x;
+    const int64_t bx = blockIdx.x;
+    const int64_t it0 = bx * per + (bx < extra ? bx : extra);
+    const int64_t it1 = it0 + per + (int64_t(blockIdx.x) < extra ? 1 : 0);
+    int64_t staged = -1;
+    for (int64_t it = it0; it < it1; ++it) {
+        const int64_t tile = it / groups;
+        const int grp = int(it - tile * groups);
+        const int64_t q0 = tile * QB;
+        const int nq = int((m - q0) < QB ? (m - q0) : int64_t(QB));
+        if (tile != staged) {
+            __syncthreads();  // the previous tile is no longer read
+            bool bad = false;
+            for (int r = warp; r < QB; r += nwarps) {
+                float *dst = qs + r * stride;
+                if (r < nq) {
+                    const float *src = Q + (q0 + r) * d;
+                    if (vec) {
+                        for (int c4 = lane; c4 < (d >> 2); c4 += 32) {
+                            const float4 x = __ldg(reinterpret_cast<const float4 *>(src) + c4);
+                            bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w));
+                            dst[4 * c4 + 0] = x.x;
+                            dst[4 * c4 + 1] = x.y;
+                            dst[4 * c4 + 2] = x.z;
+                            dst[4 * c4 + 3] = x.w;
+                        }
+                    } else {
+                        for (int c = lane; c < d; c += 32) {
+                            const float x = __ldg(src + c);
+                            bad |= !isfinite(x);
+                            dst[c] = x;
+                        }
+                    }
+                } else {
+                    for (int c = lane; c < d; c += 32) dst[c] = 0.f;
+                }
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, STATUS_NONFINITE_QUERY);
+            __syncthreads();
+            staged = tile;
         }
-#pragma unroll
-        for (int q = 0; q < QT; ++q) {
-            if (proj != nullptr && q < nq) proj[(q0 + q) * ncols + c] = acc[q];
-            node[q] = 2 * node[q] + 1 + (acc[q] > sp[node[q]] ? 1 : 0);
+        const bool live = qq < nq;
+        const int t_begin = grp * ROUTE_TREES_PER_ITEM;
+        const int t_end = min(T_use, t_begin + ROUTE_TREES_PER_ITEM);
+        for (int tb = t_begin + warp * G; tb < t_end; tb += nwarps * G) {
+            const int t = tb + g;
+            const bool tree_ok = t < t_end;
+            const int tt = tree_ok ? t : t_begin;
+            const float *sp = split + int64_t(tt) * inner;
+            int64_t node = 0;
+            for (int j = 0; j < l; ++j) {
+                const int c = tt * l + j;
+                const int e1 = __ldg(col_off + c + 1);
+                int e = __ldg(col_off + c);
+                float acc = 0.0f;
+                for (; e + 4 <= e1; e += 4) {
+                    const int d0 = __ldg(dim + e), d1 = __ldg(dim + e + 1);
+                    const int d2 = __ldg(dim + e + 2), d3 = __ldg(dim + e + 3);
+                    const float v0 = __ldg(val + e), v1 = __ldg(val + e + 1);
+                    const float v2 = __ldg(val + e + 2), v3 = __ldg(val + e + 3);
+                    const float x0 = qrow[d0], x1 = qrow[d1], x2 = qrow[d2], x3 = qrow[d3];
+                    acc = __fmaf_rn(x0, v0, acc);
+                    acc = __fmaf_rn(x1, v1, acc);
+                    acc = __fmaf_rn(x2, v2, acc);
+                    acc = __fmaf_rn(x3, v3, acc);
+                }
+                for (; e < e1; ++e) acc = __fmaf_rn(qrow[__ldg(dim + e)], __ldg(val + e), acc);
+                if (proj != nullptr && live && tree_ok) proj[(q0 + qq) * ncols + c] = acc;
+                node = 2 * node + 1 + (acc > __ldg(sp + node) ? 1 : 0);
+            }
+            if (live && tree_ok) leaf[(q0 + qq) * T_use + t] = int32_t(node - inner);
         }
     }
-#pragma unroll
-    for (int q = 0; q < QT; ++q)
-        if (q < nq) leaf[(q0 + q) * T_use + t] = int32_t(node[q] - inner);
 }
 
 // ---------------------------------------------------------- vote search ----
@@ -158,20 +212,44 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-// Squared Euclidean distance between the staged query and row `id`.
-__device__ __forceinline__ float row_sq_dist(const float4 *__restrict__ row,
-                                             const float4 *__restrict__ q4, int nv4, int lane) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int j = lane; j < nv4; j += 32) {
-        const float4 x = __ldg(row + j);
-        const float4 q = q4[j];
-        const float dx = q.x - x.x, dy = q.y - x.y, dz = q.z - x.z, dw = q.w - x.w;
-        a0 = __fmaf_rn(dx, dx, a0);
-        a1 = __fmaf_rn(dy, dy, a1);
-        a2 = __fmaf_rn(dz, dz, a2);
-        a3 = __fmaf_rn(dw, dw, a3);
+// Squared Euclidean distances between the staged query and R rows (R <= 2):
+// every lane keeps up to 4 float4 loads per row in flight before it
+// accumulates, then the warp reduces each row's partial sums.
+template <int R>
+__device__ __forceinline__ void rows_sq_dist(const float4 *const (&rows)[2],
+                                             const float4 *__restrict__ q4, int nv4, int lane,
+                                             float (&out)[2]) {
+    float acc[R][2];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r][0] = acc[r][1] = 0.f;
+    for (int base = lane; base < nv4; base += 128) {
+        float4 x[R][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = base + 32 * u;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                x[r][u] = (j < nv4) ? __ldg(rows[r] + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = base + 32 * u;
+            if (j < nv4) {
+                const float4 q = q4[j];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dx = q.x - x[r][u].x, dy = q.y - x[r][u].y;
+                    const float dz = q.z - x[r][u].z, dw = q.w - x[r][u].w;
+                    acc[r][0] = __fmaf_rn(dx, dx, acc[r][0]);
+                    acc[r][1] = __fmaf_rn(dy, dy, acc[r][1]);
+                    acc[r][0] = __fmaf_rn(dz, dz, acc[r][0]);
+                    acc[r][1] = __fmaf_rn(dw, dw, acc[r][1]);
+                }
+            }
+        }
     }
-    return warp_sum((a0 + a1) + (a2 + a3));
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = warp_sum(acc[r][0] + acc[r][1]);
 }
 
 struct VoteSearchArgs {
@@ -221,6 +299,7 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
     int32_t *wbuf = reinterpret_cast<int32_t *>(qv + a.dpad);                  // VS_WARPS * WBUF
     int32_t *cur = wbuf + VS_WARPS * WBUF;                                      // T_use
     int32_t *lend = cur + a.T_use;                                              // T_use
+    int32_t *cend = lend + a.T_use;                                             // T_use
     // merge area (aliases the counters once voting is over)
     float *md = reinterpret_cast<float *>(smem);                                // VS_WARPS * KR*32
     int32_t *mi = reinterpret_cast<int32_t *>(smem + VS_WARPS * KR * 32 * 4);
@@ -266,14 +345,18 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
             for (; j + 1 < nb; j += 2) {
                 const int32_t id0 = mybuf[j];
                 const int32_t id1 = mybuf[j + 1];
-                const float d0 = row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane);
-                const float d1 = row_sq_dist(X4 + int64_t(id1) * nv4, q4, nv4, lane);
-                top.insert(d0, id0, k, lane);
-                top.insert(d1, id1, k, lane);
+                const float4 *rows[2] = {X4 + int64_t(id0) * nv4, X4 + int64_t(id1) * nv4};
+                float dd[2];
+                rows_sq_dist<2>(rows, q4, nv4, lane, dd);
+                top.insert(dd[0], id0, k, lane);
+                top.insert(dd[1], id1, k, lane);
             }
             if (j < nb) {
                 const int32_t id0 = mybuf[j];
-                top.insert(row_sq_dist(X4 + int64_t(id0) * nv4, q4, nv4, lane), id0, k, lane);
+                const float4 *rows[2] = {X4 + int64_t(id0) * nv4, X4 + int64_t(id0) * nv4};
+                float dd[2];
+                rows_sq_dist<1>(rows, q4, nv4, lane, dd);
+                top.insert(dd[0], id0, k, lane);
             }
             __syncwarp();
         };
@@ -286,55 +369,97 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
                 const int n4 = (nwords + 3) >> 2;
                 for (int w = tid; w < n4; w += VS_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
             }
-            __syncthreads();
             const int64_t lim = c0 + CH_IDS;
-            int nb = 0;
-            for (int t = warp; t < a.T_use; t += VS_WARPS) {
-                const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
-                int32_t p = cur[t];
-                const int32_t e = lend[t];
-                while (p < e) {
-                    int32_t id[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int32_t i = p + 32 * u + lane;
-                        id[u] = (i < e) ? __ldg(ids + i) : SENTINEL_ID;
+            // end of each tree's ids inside this chunk: leaves list ids in
+            // ascending order, so it is a lower bound of `lim`
+            for (int t = tid; t < a.T_use; t += VS_THREADS) {
+                int32_t lo = cur[t], hi = lend[t];
+                if (lim < a.n) {
+                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (int64_t(__ldg(ids + mid)) < lim)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
                     }
-                    int adv = 0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const bool ok = int64_t(id[u]) < lim;
-                        bool emit = false;
-                        if (ok) {
-                            const uint32_t off = uint32_t(int64_t(id[u]) - c0);
-                            const uint32_t sh = (off & 3u) * 8u;
-                            const uint32_t old = atomicAdd(&cnt[off >> 2], 1u << sh);
-                            emit = ((old >> sh) & 0xffu) == vm1;
-                        }
-                        adv += __popc(__ballot_sync(0xffffffffu, ok));
-                        const unsigned em = __ballot_sync(0xffffffffu, emit);
-                        if (em) {
-                            if (emit) mybuf[nb + __popc(em & lt)] = id[u];
-                            if (track) {
-                                unsigned long long base = 0;
-                                if (lane == 0) base = atomicAdd(&s_total, (unsigned long long)__popc(em));
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                if (emit && a.dbg_cand != nullptr) {
-                                    const int64_t slot = int64_t(base) + __popc(em & lt);
-                                    if (slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = id[u];
-                                }
-                            }
-                            nb += __popc(em);
-                        }
-                    }
-                    if (nb >= 64) {
-                        drain(nb);
-                        nb = 0;
-                    }
-                    p += adv;
-                    if (adv < 128) break;
+                    cend[t] = lo;
+                } else {
+                    cend[t] = hi;
                 }
-                if (lane == 0) cur[t] = p;
+            }
+            __syncthreads();
+            int nb = 0;
+            // the warp's tiles (128 consecutive ids of one tree's leaf) in
+            // order; the next tile is loaded while the current one votes
+            int t = warp;
+            int32_t p = 0, e = 0;
+            while (t < a.T_use) {
+                p = cur[t];
+                e = cend[t];
+                if (p < e) break;
+                t += VS_WARPS;
+            }
+            int32_t id[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t i = p + 32 * u + lane;
+                id[u] = (t < a.T_use && i < e) ? __ldg(a.leaf_ids + int64_t(t) * a.n + i) : -1;
+            }
+            while (t < a.T_use) {
+                // position and prefetch of the next tile
+                int tn = t;
+                int32_t pn = p + 128, en = e;
+                if (pn >= en) {
+                    if (lane == 0) cur[t] = en;
+                    tn = t + VS_WARPS;
+                    while (tn < a.T_use) {
+                        pn = cur[tn];
+                        en = cend[tn];
+                        if (pn < en) break;
+                        tn += VS_WARPS;
+                    }
+                }
+                int32_t idn[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t i = pn + 32 * u + lane;
+                    idn[u] = (tn < a.T_use && i < en) ? __ldg(a.leaf_ids + int64_t(tn) * a.n + i) : -1;
+                }
+                // votes of the current tile
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bool emit = false;
+                    if (id[u] >= 0) {
+                        const uint32_t off = uint32_t(int64_t(id[u]) - c0);
+                        const uint32_t sh = (off & 3u) * 8u;
+                        const uint32_t old = atomicAdd(&cnt[off >> 2], 1u << sh);
+                        emit = ((old >> sh) & 0xffu) == vm1;
+                    }
+                    const unsigned em = __ballot_sync(0xffffffffu, emit);
+                    if (em) {
+                        if (emit) mybuf[nb + __popc(em & lt)] = id[u];
+                        if (track) {
+                            unsigned long long base = 0;
+                            if (lane == 0) base = atomicAdd(&s_total, (unsigned long long)__popc(em));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (emit && a.dbg_cand != nullptr) {
+                                const int64_t slot = int64_t(base) + __popc(em & lt);
+                                if (slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                            }
+                        }
+                        nb += __popc(em);
+                    }
+                }
+                if (nb >= 64) {
+                    drain(nb);
+                    nb = 0;
+                }
+                t = tn;
+                p = pn;
+                e = en;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) id[u] = idn[u];
             }
             if (nb > 0) drain(nb);
             __syncthreads();
@@ -408,16 +533,26 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
 
 namespace {
 
-template <int QT>
+template <int QB>
 cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const size_t smem = size_t(QT) * size_t(idx->d) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_query_route<QT>,
+    const size_t smem = size_t(QB) * size_t(idx->d | 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_query_route<QB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    const dim3 grid(unsigned((ql.m + QT - 1) / QT), unsigned((ql.n_trees + 127) / 128));
-    k_query_route<QT><<<grid, 128, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l, idx->L,
-                                              idx->col_off, idx->dim, idx->val, idx->split,
-                                              ql.leaf, ql.proj, idx->status);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query_route<QB>, 512, smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (ql.m + QB - 1) / QB;
+    const int64_t groups = (ql.n_trees + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM;
+    const int64_t items = tiles * groups;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(sms) * std::max(per_sm, 1)));
+    k_query_route<QB><<<unsigned(blocks), 512, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l,
+                                                         idx->L, idx->col_off, idx->dim, idx->val,
+                                                         idx->split, ql.leaf, ql.proj, idx->status,
+                                                         items);
     return cudaGetLastError();
 }
 
@@ -431,7 +566,7 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
     region = (region + 15) & ~size_t(15);
     const size_t smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 +
-                        size_t(2 * ql.n_trees) * 4;
+                        size_t(3 * ql.n_trees) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -482,11 +617,16 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
             if (!idx->ev[i]) MRPT_CUDA_TRY(cudaEventCreate(&idx->ev[i]));
         MRPT_CUDA_TRY(cudaEventRecord(idx->ev[0], s));
     }
-    if (per_q * 8 <= 96 * 1024)
+    // as many queries per block (up to 32, one per lane) as fit in ~110 KB
+    if (per_q * 32 <= 110 * 1024)
+        e = launch_route<32>(idx, ql, s);
+    else if (per_q * 16 <= 110 * 1024)
+        e = launch_route<16>(idx, ql, s);
+    else if (per_q * 8 <= 160 * 1024)
         e = launch_route<8>(idx, ql, s);
-    else if (per_q * 4 <= 96 * 1024)
+    else if (per_q * 4 <= 160 * 1024)
         e = launch_route<4>(idx, ql, s);
-    else if (per_q * 2 <= 160 * 1024)
+    else if (per_q * 2 <= 200 * 1024)
         e = launch_route<2>(idx, ql, s);
     else
         e = launch_route<1>(idx, ql, s);
