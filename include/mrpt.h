@@ -166,6 +166,37 @@ int64_t mrpt_export_size(const mrpt_index *idx, int32_t what);
  * Synchronous. */
 int mrpt_export(const mrpt_index *idx, int32_t what, void *dst, int64_t dst_bytes);
 
+/*
+ * mrpt_query_noalloc -- mrpt_query that allocates nothing.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *
+ * mrpt_query grows scratch buffers with cudaMalloc on first use.  Callers
+ * that cannot allocate -- a serving loop with a latency budget (cudaMalloc
+ * and cudaFree may synchronise the device), or a process whose device
+ * memory is owned or capped by another framework's pool -- use this entry
+ * point instead.  It runs the same kernels; its scratch (the leaf of each
+ * query in each tree, and the counter that hands queries to blocks) lives in
+ * one fixed 4 MiB array that every GPU loading this library holds until the
+ * process exits.
+ *
+ *   Q, out_ids, out_dists   device memory only (m x d, m x k, m x k), as in
+ *                           mrpt_query; host pointers are rejected.
+ *   n_trees                 use the first n_trees trees (0 = all T).
+ *   limit                   m * n_trees <= MRPT_NOALLOC_MAX_LEAF_ENTRIES;
+ *                           larger batches are rejected with INVALID_ARG
+ *                           (split the batch).
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.
+ * Every call, from any index or stream, shares the one array: the work
+ * counter is cleared at the start of each call, and calls whose GPU work
+ * overlaps in time race on the array.  Stream-ordered on the index's stream;
+ * no device-side status is latched beyond mrpt_query's (see mrpt_sync).
+ * Errors: INVALID_ARG, CUDA.
+ */
+#define MRPT_NOALLOC_MAX_LEAF_ENTRIES 1048512 /* (4 MiB - 256 B) / 4 */
+int mrpt_query_noalloc(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
+                       int32_t n_trees, int32_t *out_ids, float *out_dists);
+
 /* Fault injection for tests: make the allocation after the next `after`
  * successful ones fail with MRPT_ERR_OOM (negative disables).  Host-side
  * only; process-wide. */

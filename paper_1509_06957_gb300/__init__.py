@@ -50,8 +50,9 @@ EXPORT = {
 ABI_SYMBOLS = (
     "mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
-    "mrpt_debug_fail_alloc_after",
+    "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc",
 )
+MRPT_NOALLOC_MAX_LEAF_ENTRIES = 1048512
 
 
 class MRPTError(RuntimeError):
@@ -132,6 +133,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_export.argtypes = [vp, i32, vp, i64]
         lib.mrpt_debug_fail_alloc_after.restype = ctypes.c_int
         lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
+        lib.mrpt_query_noalloc.restype = ctypes.c_int
+        lib.mrpt_query_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp]
         _lib = lib
         return lib
 
@@ -345,3 +348,18 @@ def mrpt_export(index: Index, what: str) -> np.ndarray:
 
 def mrpt_debug_fail_alloc_after(after: int) -> None:
     _check(load_library().mrpt_debug_fail_alloc_after(int(after)))
+
+
+def mrpt_query_noalloc(index: Index, Q, k: int, v: int, out_ids, out_dists,
+                       n_trees: int = 0) -> None:
+    """mrpt_query without any device allocation, for callers that may not
+    allocate (a latency-bound serving loop, or device memory owned by
+    another framework's pool).  Q, out_ids and out_dists must be CUDA
+    tensors; m * n_trees is limited to MRPT_NOALLOC_MAX_LEAF_ENTRIES; calls
+    whose GPU work overlaps share one scratch array and race."""
+    lib = load_library()
+    stream = _current_stream(Q)
+    if stream is not None:
+        _check(lib.mrpt_set_stream(index.handle, stream))
+    _check(lib.mrpt_query_noalloc(index.handle, _ptr(Q), Q.shape[0], k, v, int(n_trees),
+                                  _ptr(out_ids), _ptr(out_dists)))

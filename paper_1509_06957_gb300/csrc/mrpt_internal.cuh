@@ -119,4 +119,8 @@ struct QueryLaunch {
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);
 
+// launch_query with caller-supplied scratch: ql.leaf holds the m x n_trees
+// leaf-of-query table and `work` the work counter.
+int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *work);
+
 }  // namespace mrpt

@@ -605,6 +605,51 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     return cudaGetLastError();
 }
 
+// As launch_vote, with the work counter at `work` (cleared here).
+template <int KR>
+cudaError_t launch_vote_with_counter(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s,
+                                     uint32_t *work) {
+    const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
+    const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
+    const size_t merge_bytes = size_t(VS_WARPS) * KR * 32 * 8;
+    size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
+    region = (region + 15) & ~size_t(15);
+    const size_t smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 +
+                        size_t(3 * ql.n_trees) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_search<KR>, VS_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
+    VoteSearchArgs a{};
+    a.X = idx->X;
+    a.n = idx->n;
+    a.dpad = idx->dpad;
+    a.Q = ql.Q;
+    a.m = ql.m;
+    a.d = idx->d;
+    a.leaf_of_q = ql.leaf;
+    a.T_use = ql.n_trees;
+    a.leaf_off = idx->leaf_off;
+    a.leaf_ids = idx->leaf_ids;
+    a.k = ql.k;
+    a.v = ql.v;
+    a.out_ids = ql.out_ids;
+    a.out_dists = ql.out_dists;
+    a.work = work;
+    a.cnt_words = cnt_words;
+    a.region_bytes = int(region);
+    e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
@@ -649,6 +694,44 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
         MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[1], idx->ev[1], idx->ev[2]));
         MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[2], idx->ev[0], idx->ev[2]));
     }
+    return MRPT_OK;
+}
+
+}  // namespace mrpt
+
+namespace mrpt {
+
+// The same two kernels as launch_query, with the leaf-of-query table in
+// ql.leaf and the work counter at `work`, both supplied by the caller; no
+// stage timing.  Used by the allocation-free entry point.
+int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *work) {
+    cudaStream_t s = idx->stream;
+    if (ql.m == 0) return MRPT_OK;
+    const int64_t per_q = int64_t(idx->d) * 4;
+    cudaError_t e;
+    if (per_q * 32 <= 110 * 1024)
+        e = launch_route<32>(idx, ql, s);
+    else if (per_q * 16 <= 110 * 1024)
+        e = launch_route<16>(idx, ql, s);
+    else if (per_q * 8 <= 160 * 1024)
+        e = launch_route<8>(idx, ql, s);
+    else if (per_q * 4 <= 160 * 1024)
+        e = launch_route<4>(idx, ql, s);
+    else if (per_q * 2 <= 200 * 1024)
+        e = launch_route<2>(idx, ql, s);
+    else
+        e = launch_route<1>(idx, ql, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    const int kr = (ql.k + 31) / 32;
+    if (kr <= 1)
+        e = launch_vote_with_counter<1>(idx, ql, s, work);
+    else if (kr <= 2)
+        e = launch_vote_with_counter<2>(idx, ql, s, work);
+    else if (kr <= 4)
+        e = launch_vote_with_counter<4>(idx, ql, s, work);
+    else
+        e = launch_vote_with_counter<8>(idx, ql, s, work);
+    if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
     return MRPT_OK;
 }
 
