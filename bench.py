@@ -122,23 +122,33 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def source_sha(paths):
-    h = hashlib.sha256()
-    for p in paths:
-        h.update(open(p, "rb").read())
-    return h.hexdigest()[:16]
+def kernel_source_sha(kernel: str, path: str) -> str:
+    """Hash of one kernel's source: the lines from its `__global__`
+    declaration to the next top-level closing brace."""
+    lines = open(path).read().split("\n")
+    start = None
+    for i, ln in enumerate(lines):
+        if "__global__" in ln and (kernel + "(") in " ".join(lines[i:i + 2]):
+            start = i
+            break
+    if start is None:
+        return ""
+    end = start
+    while end < len(lines) and lines[end] != "}":
+        end += 1
+    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
 
 
-def load_traffic(kernel_src):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "vote_search_mnist60k.json")
+def load_traffic(kernel: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if
+    it was taken on the kernel's current source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    j = json.load(open(p))
-    if j.get("source_sha") != source_sha(kernel_src):
+    entry = json.load(open(p)).get(kernel)
+    if not entry or entry.get("source_sha") != kernel_source_sha(kernel, src):
         return None
-    return j.get("dram_bytes_per_launch")
+    return entry.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------- ground truth -----
@@ -216,12 +226,12 @@ def run_gpu(args):
 
     def query(T_use, v, stage=None):
         mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, out_ids=ids, out_dists=dists,
-                         stage_ms=stage)
+                         stage_ms=stage, path=args.path)
 
     # ---- sweep (T, v): fastest with recall >= target (tie-aware), unless
     # the operating point is given
     sweep = []
-    stage = np.zeros(3, np.float32)
+    stage = np.zeros(4, np.float32)
     grid = [(args.T, args.v)] if args.T and args.v else \
         [(T_, v_) for T_ in W["T_grid"] for v_ in W["v_grid"] if v_ <= T_]
     for T_use, v in grid:
@@ -229,7 +239,7 @@ def run_gpu(args):
         flush.zero_()
         query(T_use, v, stage)
         rs, rt = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
-        sweep.append(dict(T=T_use, v=v, ms=float(stage[2]), recall=round(rt, 4),
+        sweep.append(dict(T=T_use, v=v, ms=float(stage[3]), recall=round(rt, 4),
                           recall_strict=round(rs, 4)))
     ok = [s for s in sweep if s["recall"] >= W["target_recall"]]
     best = min(ok, key=lambda s: s["ms"]) if ok else max(sweep, key=lambda s: s["recall"])
@@ -244,7 +254,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         query(T_use, v)
     torch.cuda.synchronize()
-    per_step, vote_ms, route_ms = [], [], []
+    per_step, vote_ms, route_ms, search_ms = [], [], [], []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -254,7 +264,8 @@ def run_gpu(args):
             query(T_use, v, stage)
             route_ms.append(float(stage[0]))
             vote_ms.append(float(stage[1]))
-            per_step.append(float(stage[2]))
+            search_ms.append(float(stage[2]))
+            per_step.append(float(stage[3]))
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -273,23 +284,41 @@ def run_gpu(args):
     if not args.no_e2e:
         e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch)
 
-    # ---- roofline of the dominant kernel (vote/search)
+    # ---- rooflines: voting (leaf ids, L2-resident) and candidate search
+    # (candidate rows); "roofline" reports the kernel that takes longer
     peak, peak_kind = load_peaks()
     L = 1 << l
     leaf_bytes = T_use * math.ceil(n / L) * 4
-    cand_bytes = mean_S * d * 4
-    per_query = leaf_bytes + cand_bytes + d * 4 + T_use * 4 + k * 8
-    vote_avg_ms = statistics.mean(vote_ms)
-    achieved = per_query * m / (vote_avg_ms / 1e3) / 1e9
-    kernel_src = [os.path.join(ROOT, "paper_1509_06957_gb300", "csrc", "mrpt_query.cu")]
-    traffic = load_traffic(kernel_src)
-    dedup = (leaf_bytes + d * 4 + T_use * 4 + k * 8) * m + min(n, mean_S * m) * d * 4
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_kind": f"{peak_kind} hbm_gbs",
-                "kernel": "k_vote_search",
-                "algorithmic_bytes_per_query": round(per_query, 1),
-                "frac_dedup_rows": round(dedup / (vote_avg_ms / 1e3) / 1e9 / peak, 4)}
+    row_bytes = mean_S * d * 4
+    vote_avg = statistics.mean(vote_ms)
+    search_avg = statistics.mean(search_ms)
+    if args.path == 1:
+        # one fused kernel reads both
+        vote_bytes = leaf_bytes + row_bytes + d * 4 + T_use * 4 + k * 8
+        search_bytes = 0.0
+    else:
+        vote_bytes = leaf_bytes + T_use * 4 + mean_S * 4 + 4
+        search_bytes = row_bytes + mean_S * 4 + d * 4 + k * 8 + 4
+    src = os.path.join(ROOT, "paper_1509_06957_gb300", "csrc", "mrpt_query.cu")
+
+    def roof(name, per_query, ms):
+        achieved = per_query * m / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": load_traffic(name, src),
+                "peak_kind": f"{peak_kind} hbm_gbs", "kernel": name,
+                "algorithmic_bytes_per_query": round(per_query, 1), "avg_ms": round(ms, 4)}
+
+    r_vote = roof("k_vote_search" if args.path == 1 else "k_vote_emit", vote_bytes, vote_avg)
+    rooflines = [r_vote]
+    if args.path == 0:
+        r_search = roof("k_cand_knn", search_bytes, search_avg)
+        # each candidate row once per step (rows reused across queries)
+        uniq = min(n, mean_S * m) * d * 4
+        r_search["frac_rows_once"] = round(
+            (uniq + (search_bytes - row_bytes) * m) / (search_avg / 1e3) / 1e9 / peak, 4)
+        rooflines.append(r_search)
+    roofline = max(rooflines, key=lambda r: r["avg_ms"])
+    others = [r for r in rooflines if r is not roofline]
 
     out = None
     if rank == 0:
@@ -305,14 +334,16 @@ def run_gpu(args):
                        "recall_at_10_strict": round(recall_strict, 4),
                        "mean_candidates": round(mean_S, 1), "build_s_T200": round(build_s, 3),
                        "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "path": "fused" if args.path == 1 else "vote-emit + candidate-search"},
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (2 if args.path == 1 else 4) * args.steps,
             "roofline": roofline,
+            "roofline_other_kernels": others,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "stage_ms": {"route": round(statistics.mean(route_ms), 4),
-                         "vote_search": round(vote_avg_ms, 4)},
+                         "vote": round(vote_avg, 4), "search": round(search_avg, 4)},
             "sweep": sweep,
         }
         print(json.dumps(out), flush=True)
@@ -441,6 +472,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--path", type=int, default=0, choices=[0, 1],
+                    help="0: vote/emit + candidate search kernels, 1: one fused kernel")
     ap.add_argument("--T", type=int, default=0, help="fix the number of trees (with --v)")
     ap.add_argument("--v", type=int, default=0, help="fix the vote threshold (with --T)")
     ap.add_argument("--ref-T", type=int, default=100)

@@ -105,7 +105,8 @@ int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
  * and set what is needed.  Debug pointers are device or host buffers. */
 typedef struct mrpt_query_opts {
     int32_t n_trees;      /* use the first n_trees trees (0 = all T) */
-    int32_t reserved0;
+    int32_t path;         /* 0: vote/emit kernel + candidate-search kernel (default);
+                             1: one fused vote + search kernel.  Same results. */
     /* debug outputs (NULL = not written) */
     float *proj;          /* m x (n_trees*l): p = q^T R per tree and level (Algorithm 3) */
     int32_t *leaf;        /* m x n_trees: the query's leaf in each tree */
@@ -113,9 +114,11 @@ typedef struct mrpt_query_opts {
     int64_t *n_cand;      /* m: |S| */
     int32_t *cand;        /* m x cand_cap: members of S (any order) */
     int64_t cand_cap;     /* row capacity of `cand`; members past it are dropped */
-    /* host float[3] (NULL = not measured): device time in ms of the routing
-     * kernel, of the vote/search kernel and of the whole query, from CUDA
-     * events recorded on the index's stream; the call then synchronises */
+    /* host float[4] (NULL = not measured): device time in ms of routing,
+     * of voting (path 0: the vote/emit kernel; path 1: the fused kernel), of
+     * the candidate search (path 0; 0 for path 1) and of the whole query,
+     * from CUDA events recorded on the index's stream; the call then
+     * synchronises */
     float *stage_ms;
 } mrpt_query_opts;
 

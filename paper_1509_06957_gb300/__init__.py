@@ -64,7 +64,7 @@ class MRPTError(RuntimeError):
 class QueryOpts(ctypes.Structure):
     _fields_ = [
         ("n_trees", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("path", ctypes.c_int32),
         ("proj", ctypes.c_void_p),
         ("leaf", ctypes.c_void_p),
         ("votes", ctypes.c_void_p),
@@ -271,13 +271,14 @@ def mrpt_info(index: Index) -> IndexInfo:
 
 def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
                   out_dists=None, debug: bool = False, cand_cap: int | None = None,
-                  stage_ms=None):
+                  stage_ms=None, path: int = 0):
     """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
     tensors for a CUDA tensor, numpy arrays for host input) unless given.
     With ``debug`` also returns a dict of the internals: proj, leaf, votes,
     n_cand and cand (members of S, row padded).  ``stage_ms`` (a float32
-    numpy array of 3) receives the routing, vote/search and total device
-    times of this call in ms."""
+    numpy array of 4) receives the routing, voting, candidate-search and
+    total device times of this call in ms.  ``path`` 0 runs the vote/emit
+    and candidate-search kernels, 1 the fused kernel."""
     lib = load_library()
     Q = _as_f32(Q)
     m = Q.shape[0]
@@ -290,8 +291,9 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
         _check(lib.mrpt_set_stream(index.handle, stream))
     opts = QueryOpts()
     opts.n_trees = int(n_trees)
+    opts.path = int(path)
     if stage_ms is not None:
-        assert stage_ms.dtype == np.float32 and stage_ms.size >= 3
+        assert stage_ms.dtype == np.float32 and stage_ms.size >= 4
         opts.stage_ms = stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     dbg = None
     if debug:

@@ -15,6 +15,9 @@ namespace mrpt {
 
 namespace {
 thread_local std::string g_last_error;
+// Longest candidate list per query kept for the two-kernel query path;
+// queries with more candidates are answered by the fused kernel.
+constexpr int64_t kCandListCap = 2048;
 std::atomic<int32_t> g_fail_after{-1};
 }  // namespace
 
@@ -93,6 +96,7 @@ static void free_index(mrpt_index *idx) {
     idx->q_stage.release();
     idx->o_stage.release();
     idx->dbg_stage.release();
+    idx->q_cand.release();
     delete idx;
 }
 
@@ -193,10 +197,10 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
     if ((rc = dev_alloc((void **)&idx->split, sbytes, "split values"))) return fail(rc);
     if ((rc = dev_alloc((void **)&idx->leaf_off, size_t(idx->L + 1) * sizeof(int32_t), "leaf offsets")))
         return fail(rc);
-    if ((rc = dev_alloc((void **)&idx->status, 4 * sizeof(uint32_t), "status words"))) return fail(rc);
-    idx->device_bytes += int64_t(sbytes + size_t(idx->L + 1) * 4 + 16);
+    if ((rc = dev_alloc((void **)&idx->status, 8 * sizeof(uint32_t), "status words"))) return fail(rc);
+    idx->device_bytes += int64_t(sbytes + size_t(idx->L + 1) * 4 + 32);
     {
-        cudaError_t e = cudaMemset(idx->status, 0, 4 * sizeof(uint32_t));
+        cudaError_t e = cudaMemset(idx->status, 0, 8 * sizeof(uint32_t));
         if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: status"));
     }
     if ((rc = grow_trees_device(idx))) return fail(rc);
@@ -260,7 +264,8 @@ int mrpt_info(const mrpt_index *idx, mrpt_index_info *info) {
     info->seed = idx->seed;
     info->nnz = idx->nnz;
     info->device_bytes = idx->device_bytes + int64_t(idx->q_leaf.bytes + idx->q_stage.bytes +
-                                                     idx->o_stage.bytes + idx->dbg_stage.bytes);
+                                                     idx->o_stage.bytes + idx->dbg_stage.bytes +
+                                                     idx->q_cand.bytes);
     return MRPT_OK;
 }
 
@@ -357,6 +362,21 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
     if (!ql.leaf) {
         if ((rc = idx->q_leaf.ensure(leaf_b, "leaf-of-query scratch"))) return rc;
         ql.leaf = static_cast<int32_t *>(idx->q_leaf.ptr);
+    }
+    ql.path = opts ? opts->path : 0;
+    if (ql.path == 0) {
+        // |S| <= T ceil(n / 2^l) / v (Sec. III-B: every member of S holds at
+        // least v of the T ceil(n / 2^l) votes), and |S| <= n
+        const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
+        int64_t bound = int64_t(n_trees) * leaf_max / v;
+        if (bound > idx->n) bound = idx->n;
+        ql.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
+        if (ql.capq < 1) ql.capq = 1;
+        const size_t lb = size_t(m) * size_t(ql.capq) * 4;
+        if ((rc = idx->q_cand.ensure(lb + size_t(m) * 8, "candidate lists"))) return rc;
+        ql.cand_list = static_cast<int32_t *>(idx->q_cand.ptr);
+        ql.ncand = reinterpret_cast<int32_t *>(static_cast<char *>(idx->q_cand.ptr) + lb);
+        ql.overflow = ql.ncand + m;
     }
 
     if ((rc = launch_query(idx, ql))) return rc;

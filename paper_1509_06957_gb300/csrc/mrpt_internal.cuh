@@ -77,9 +77,10 @@ struct mrpt_index {
     mrpt::Scratch q_stage;   // staged host queries (m x d)
     mrpt::Scratch o_stage;   // staged outputs (m x k ids + m x k dists)
     mrpt::Scratch dbg_stage; // staged debug outputs
+    mrpt::Scratch q_cand;    // candidate lists, |S| per query, overflow list
 
     int64_t device_bytes = 0;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // stage timing (created on first use)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (created on first use)
 };
 
 namespace mrpt {
@@ -114,7 +115,12 @@ struct QueryLaunch {
     int64_t *n_cand;       // optional m
     int32_t *cand;         // optional m x cand_cap
     int64_t cand_cap;
-    float *stage_ms;       // optional host float[3]
+    float *stage_ms;       // optional host float[4]
+    int32_t path;          // 0: vote/emit + candidate search, 1: one fused kernel
+    int32_t *cand_list;    // m x capq candidate lists (path 0)
+    int32_t capq;
+    int32_t *ncand;        // m (path 0)
+    int32_t *overflow;     // m (path 0)
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);

@@ -273,6 +273,8 @@ struct VoteSearchArgs {
     uint32_t *work;
     int32_t cnt_words;     // counter words per chunk (<= CH_WORDS, multiple of 4)
     int32_t region_bytes;  // bytes of the counter / merge region (multiple of 16)
+    const int32_t *qlist;        // optional: process only these queries ...
+    const uint32_t *qlist_len;   // ... this many of them (read on the device)
 };
 
 // Per warp: a buffer of emitted candidates waiting for their distances.
@@ -322,12 +324,19 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
 
     for (;;) {
         if (tid == 0) {
-            s_q = int64_t(atomicAdd(a.work, 1u));
+            const uint32_t w = atomicAdd(a.work, 1u);
+            int64_t q = -1;
+            if (a.qlist != nullptr) {
+                if (w < *a.qlist_len) q = a.qlist[w];
+            } else if (int64_t(w) < a.m) {
+                q = int64_t(w);
+            }
+            s_q = q;
             s_total = 0ull;
         }
         __syncthreads();
         const int64_t qi = s_q;
-        if (qi >= a.m) break;
+        if (qi < 0) break;
 
         for (int i = tid; i < a.dpad; i += VS_THREADS) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
         for (int t = tid; t < a.T_use; t += VS_THREADS) {
@@ -427,15 +436,20 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
                     idn[u] = (tn < a.T_use && i < en) ? __ldg(a.leaf_ids + int64_t(tn) * a.n + i) : -1;
                 }
                 // votes of the current tile
+                // every atomic of the tile is issued before any result is used
+                uint32_t olds[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    bool emit = false;
+                    olds[u] = 0u;
                     if (id[u] >= 0) {
                         const uint32_t off = uint32_t(int64_t(id[u]) - c0);
                         const uint32_t sh = (off & 3u) * 8u;
-                        const uint32_t old = atomicAdd(&cnt[off >> 2], 1u << sh);
-                        emit = ((old >> sh) & 0xffu) == vm1;
+                        olds[u] = atomicAdd(&cnt[off >> 2], 1u << sh) >> sh;
                     }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool emit = id[u] >= 0 && (olds[u] & 0xffu) == vm1;
                     const unsigned em = __ballot_sync(0xffffffffu, emit);
                     if (em) {
                         if (emit) mybuf[nb + __popc(em & lt)] = id[u];
@@ -529,6 +543,262 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
     }
 }
 
+// ------------------------------------------------- vote / emit + search ----
+//
+// The batched path splits the query in two kernels:
+//   k_vote_emit  votes (as in k_vote_search) and writes each query's
+//                candidate set S to a per-query list in global memory; it
+//                carries no distance state, so a block has 16 warps.
+//   k_cand_knn   one warp per query: exact distances of the listed
+//                candidates (128-bit row loads, two rows in flight) and the
+//                warp's sorted top-k, written straight to the output row.
+// Queries whose |S| exceeds the list capacity are appended to an overflow
+// list and answered by k_vote_search, which needs no list.
+
+constexpr int VE_THREADS = 512;
+constexpr int VE_WARPS = VE_THREADS / 32;
+
+struct VoteEmitArgs {
+    int64_t n;
+    const int32_t *leaf_of_q;
+    int32_t T_use;
+    const int32_t *leaf_off;
+    const int32_t *leaf_ids;
+    int64_t m;
+    int32_t v;
+    int32_t *cand;         // m x capq candidate ids
+    int32_t capq;
+    int32_t *ncand;        // m: |S|
+    int32_t *overflow;     // queries with |S| > capq
+    uint32_t *n_overflow;
+    uint32_t *work;
+    int32_t cnt_words;
+    uint8_t *dbg_votes;
+    int64_t *dbg_ncand;
+    int32_t *dbg_cand;
+    int64_t cand_cap;
+};
+
+__global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words
+    int32_t *cur = reinterpret_cast<int32_t *>(cnt + a.cnt_words);
+    int32_t *lend = cur + a.T_use;
+    int32_t *cend = lend + a.T_use;
+    __shared__ int64_t s_q;
+    __shared__ int s_cnt;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t vm1 = uint32_t(a.v - 1);
+
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(a.work, 1u);
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi < 0) break;
+        for (int t = tid; t < a.T_use; t += VE_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * a.T_use + t];
+            cur[t] = a.leaf_off[lf];
+            lend[t] = a.leaf_off[lf + 1];
+        }
+        int32_t *clist = a.cand + qi * int64_t(a.capq);
+        for (int64_t c0 = 0; c0 < a.n; c0 += CH_IDS) {
+            const int64_t wleft = (a.n - c0 + 3) >> 2;
+            const int nwords = int(wleft < a.cnt_words ? wleft : int64_t(a.cnt_words));
+            {
+                uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+                const int n4 = (nwords + 3) >> 2;
+                for (int w = tid; w < n4; w += VE_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            __syncthreads();  // cur/lend written, counters cleared
+            const int64_t lim = c0 + CH_IDS;
+            for (int t = tid; t < a.T_use; t += VE_THREADS) {
+                int32_t lo = cur[t], hi = lend[t];
+                if (lim < a.n) {
+                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (int64_t(__ldg(ids + mid)) < lim)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    cend[t] = lo;
+                } else {
+                    cend[t] = hi;
+                }
+            }
+            __syncthreads();
+            // the warp's 128-id tiles, the next one loaded while the current
+            // one votes
+            int t = warp;
+            int32_t p = 0, e = 0;
+            while (t < a.T_use) {
+                p = cur[t];
+                e = cend[t];
+                if (p < e) break;
+                t += VE_WARPS;
+            }
+            int32_t id[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t i = p + 32 * u + lane;
+                id[u] = (t < a.T_use && i < e) ? __ldg(a.leaf_ids + int64_t(t) * a.n + i) : -1;
+            }
+            while (t < a.T_use) {
+                int tn = t;
+                int32_t pn = p + 128, en = e;
+                if (pn >= en) {
+                    if (lane == 0) cur[t] = en;
+                    tn = t + VE_WARPS;
+                    while (tn < a.T_use) {
+                        pn = cur[tn];
+                        en = cend[tn];
+                        if (pn < en) break;
+                        tn += VE_WARPS;
+                    }
+                }
+                int32_t idn[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t i = pn + 32 * u + lane;
+                    idn[u] = (tn < a.T_use && i < en) ? __ldg(a.leaf_ids + int64_t(tn) * a.n + i) : -1;
+                }
+                uint32_t olds[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    olds[u] = 0u;
+                    if (id[u] >= 0) {
+                        const uint32_t off = uint32_t(int64_t(id[u]) - c0);
+                        const uint32_t sh = (off & 3u) * 8u;
+                        olds[u] = atomicAdd(&cnt[off >> 2], 1u << sh) >> sh;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    // Algorithm 4: a point joins S when its count becomes v
+                    const bool emit = id[u] >= 0 && (olds[u] & 0xffu) == vm1;
+                    const unsigned em = __ballot_sync(0xffffffffu, emit);
+                    if (em) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_cnt, __popc(em));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (emit) {
+                            const int slot = base + __popc(em & lt);
+                            if (slot < a.capq) clist[slot] = id[u];
+                            if (a.dbg_cand != nullptr && slot < a.cand_cap)
+                                a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                        }
+                    }
+                }
+                t = tn;
+                p = pn;
+                e = en;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) id[u] = idn[u];
+            }
+            __syncthreads();
+            if (a.dbg_votes != nullptr) {
+                for (int w = tid; w < nwords; w += VE_THREADS) {
+                    const uint32_t word = cnt[w];
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t id2 = c0 + 4 * int64_t(w) + b;
+                        if (id2 < a.n) a.dbg_votes[qi * a.n + id2] = uint8_t((word >> (8 * b)) & 0xffu);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (tid == 0) {
+            const int c = s_cnt;
+            a.ncand[qi] = c;
+            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
+            if (c > a.capq) a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
+        }
+    }
+}
+
+constexpr int CK_THREADS = 256;
+constexpr int CK_WARPS = CK_THREADS / 32;
+
+struct CandKnnArgs {
+    const float *X;
+    int32_t dpad;
+    const float *Q;
+    int64_t m;
+    int32_t d;
+    const int32_t *cand;
+    int32_t capq;
+    const int32_t *ncand;
+    int32_t k;
+    int32_t *out_ids;
+    float *out_dists;
+    uint32_t *work;
+};
+
+template <int KR>
+__global__ void __launch_bounds__(CK_THREADS) k_cand_knn(const CandKnnArgs a) {
+    extern __shared__ __align__(16) float qsm[];  // CK_WARPS x dpad
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *qv = qsm + warp * a.dpad;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+    const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
+    const int nv4 = a.dpad >> 2;
+    const int k = a.k;
+    for (;;) {
+        int64_t qi = 0;
+        if (lane == 0) qi = int64_t(atomicAdd(a.work, 1u));
+        qi = __shfl_sync(0xffffffffu, qi, 0);
+        if (qi >= a.m) break;
+        const int c = a.ncand[qi];
+        if (c > a.capq) continue;  // answered by the overflow pass
+        for (int i = lane; i < a.dpad; i += 32) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
+        __syncwarp();
+        WarpTopK<KR> top;
+        top.init();
+        const int32_t *clist = a.cand + qi * int64_t(a.capq);
+        for (int base = 0; base < c; base += 32) {
+            const int32_t mine = (base + lane < c) ? __ldg(clist + base + lane) : 0;
+            const int cb = min(32, c - base);
+            int j = 0;
+            for (; j + 1 < cb; j += 2) {
+                const int32_t id0 = __shfl_sync(0xffffffffu, mine, j);
+                const int32_t id1 = __shfl_sync(0xffffffffu, mine, j + 1);
+                const float4 *rows[2] = {X4 + int64_t(id0) * nv4, X4 + int64_t(id1) * nv4};
+                float dd[2];
+                rows_sq_dist<2>(rows, q4, nv4, lane, dd);
+                top.insert(dd[0], id0, k, lane);
+                top.insert(dd[1], id1, k, lane);
+            }
+            if (j < cb) {
+                const int32_t id0 = __shfl_sync(0xffffffffu, mine, j);
+                const float4 *rows[2] = {X4 + int64_t(id0) * nv4, X4 + int64_t(id0) * nv4};
+                float dd[2];
+                rows_sq_dist<1>(rows, q4, nv4, lane, dd);
+                top.insert(dd[0], id0, k, lane);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+            const int e = r * 32 + lane;
+            if (e < k) {
+                const bool real = top.i[r] != SENTINEL_ID;
+                a.out_ids[qi * k + e] = real ? top.i[r] : -1;
+                a.out_dists[qi * k + e] = real ? sqrtf(top.d[r]) : INFINITY;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // -------------------------------------------------------------- launch ----
 
 namespace {
@@ -556,8 +826,10 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
     return cudaGetLastError();
 }
 
+// Shared-memory plan and arguments of k_vote_search.
 template <int KR>
-cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *work,
+                      VoteSearchArgs &a, size_t &smem, int64_t &blocks) {
     // counters for min(n, CH_IDS) ids, rounded to 16 bytes; the same region
     // later holds the warps' top-k lists for the merge
     const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
@@ -565,19 +837,17 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     const size_t merge_bytes = size_t(VS_WARPS) * KR * 32 * 8;
     size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
     region = (region + 15) & ~size_t(15);
-    const size_t smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 +
-                        size_t(3 * ql.n_trees) * 4;
+    smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 + size_t(3 * ql.n_trees) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
+    int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_search<KR>, VS_THREADS, smem);
     if (e != cudaSuccess) return e;
-    int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
-    VoteSearchArgs a;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
+    a = VoteSearchArgs{};
     a.X = idx->X;
     a.n = idx->n;
     a.dpad = idx->dpad;
@@ -596,9 +866,19 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     a.dbg_ncand = ql.n_cand;
     a.dbg_cand = ql.cand;
     a.cand_cap = ql.cand_cap;
-    a.work = idx->status + 1;
+    a.work = work;
     a.cnt_words = cnt_words;
     a.region_bytes = int(region);
+    return cudaSuccess;
+}
+
+template <int KR>
+cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    VoteSearchArgs a;
+    size_t smem = 0;
+    int64_t blocks = 0;
+    cudaError_t e = plan_vote<KR>(idx, ql, idx->status + 1, a, smem, blocks);
+    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(idx->status + 1, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
@@ -609,43 +889,112 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
 template <int KR>
 cudaError_t launch_vote_with_counter(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s,
                                      uint32_t *work) {
+    VoteSearchArgs a;
+    size_t smem = 0;
+    int64_t blocks = 0;
+    cudaError_t e = plan_vote<KR>(idx, ql, work, a, smem, blocks);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace {
+
+cudaError_t launch_route_any(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    // as many queries per block (up to 32, one per lane) as fit in ~110 KB
+    const int64_t per_q = int64_t(idx->d) * 4;
+    if (per_q * 32 <= 110 * 1024) return launch_route<32>(idx, ql, s);
+    if (per_q * 16 <= 110 * 1024) return launch_route<16>(idx, ql, s);
+    if (per_q * 8 <= 160 * 1024) return launch_route<8>(idx, ql, s);
+    if (per_q * 4 <= 160 * 1024) return launch_route<4>(idx, ql, s);
+    if (per_q * 2 <= 200 * 1024) return launch_route<2>(idx, ql, s);
+    return launch_route<1>(idx, ql, s);
+}
+
+cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
     const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
     const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
-    const size_t merge_bytes = size_t(VS_WARPS) * KR * 32 * 8;
-    size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
-    region = (region + 15) & ~size_t(15);
-    const size_t smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 +
-                        size_t(3 * ql.n_trees) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const size_t smem = size_t(cnt_words) * 4 + size_t(3 * ql.n_trees) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_vote_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_search<KR>, VS_THREADS, smem);
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_emit, VE_THREADS, smem);
     if (e != cudaSuccess) return e;
-    int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
-    VoteSearchArgs a{};
-    a.X = idx->X;
+    VoteEmitArgs a{};
     a.n = idx->n;
-    a.dpad = idx->dpad;
-    a.Q = ql.Q;
-    a.m = ql.m;
-    a.d = idx->d;
     a.leaf_of_q = ql.leaf;
     a.T_use = ql.n_trees;
     a.leaf_off = idx->leaf_off;
     a.leaf_ids = idx->leaf_ids;
-    a.k = ql.k;
+    a.m = ql.m;
     a.v = ql.v;
+    a.cand = ql.cand_list;
+    a.capq = ql.capq;
+    a.ncand = ql.ncand;
+    a.overflow = ql.overflow;
+    a.n_overflow = idx->status + 3;
+    a.work = idx->status + 1;
+    a.cnt_words = cnt_words;
+    a.dbg_votes = ql.votes;
+    a.dbg_ncand = ql.n_cand;
+    a.dbg_cand = ql.cand;
+    a.cand_cap = ql.cand_cap;
+    k_vote_emit<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KR>
+cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    const size_t smem = size_t(CK_WARPS) * size_t(idx->dpad) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_cand_knn<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR>, CK_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(
+        1, std::min<int64_t>((ql.m + CK_WARPS - 1) / CK_WARPS, int64_t(sms) * std::max(per_sm, 1)));
+    CandKnnArgs a{};
+    a.X = idx->X;
+    a.dpad = idx->dpad;
+    a.Q = ql.Q;
+    a.m = ql.m;
+    a.d = idx->d;
+    a.cand = ql.cand_list;
+    a.capq = ql.capq;
+    a.ncand = ql.ncand;
+    a.k = ql.k;
     a.out_ids = ql.out_ids;
     a.out_dists = ql.out_dists;
-    a.work = work;
-    a.cnt_words = cnt_words;
-    a.region_bytes = int(region);
-    e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
+    a.work = idx->status + 2;
+    k_cand_knn<KR><<<unsigned(blocks), CK_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// k_vote_search over the overflow list (its length is read on the device).
+template <int KR>
+cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    VoteSearchArgs a;
+    size_t smem = 0;
+    int64_t blocks = 0;
+    QueryLaunch q2 = ql;
+    q2.votes = nullptr;
+    q2.n_cand = nullptr;
+    q2.cand = nullptr;
+    cudaError_t e = plan_vote<KR>(idx, q2, idx->status + 4, a, smem, blocks);
     if (e != cudaSuccess) return e;
+    a.qlist = ql.overflow;
+    a.qlist_len = idx->status + 3;
     k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -655,44 +1004,61 @@ cudaError_t launch_vote_with_counter(const mrpt_index *idx, const QueryLaunch &q
 int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     cudaStream_t s = idx->stream;
     if (ql.m == 0) return MRPT_OK;
-    const int64_t per_q = int64_t(idx->d) * 4;
     cudaError_t e;
     if (ql.stage_ms) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 4; ++i)
             if (!idx->ev[i]) MRPT_CUDA_TRY(cudaEventCreate(&idx->ev[i]));
         MRPT_CUDA_TRY(cudaEventRecord(idx->ev[0], s));
     }
-    // as many queries per block (up to 32, one per lane) as fit in ~110 KB
-    if (per_q * 32 <= 110 * 1024)
-        e = launch_route<32>(idx, ql, s);
-    else if (per_q * 16 <= 110 * 1024)
-        e = launch_route<16>(idx, ql, s);
-    else if (per_q * 8 <= 160 * 1024)
-        e = launch_route<8>(idx, ql, s);
-    else if (per_q * 4 <= 160 * 1024)
-        e = launch_route<4>(idx, ql, s);
-    else if (per_q * 2 <= 200 * 1024)
-        e = launch_route<2>(idx, ql, s);
-    else
-        e = launch_route<1>(idx, ql, s);
+    e = launch_route_any(idx, ql, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
     if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[1], s));
     const int kr = (ql.k + 31) / 32;
-    if (kr <= 1)
-        e = launch_vote<1>(idx, ql, s);
-    else if (kr <= 2)
-        e = launch_vote<2>(idx, ql, s);
-    else if (kr <= 4)
-        e = launch_vote<4>(idx, ql, s);
-    else
-        e = launch_vote<8>(idx, ql, s);
-    if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
+    if (ql.path == 1 || ql.cand_list == nullptr) {
+        // one fused kernel
+        if (kr <= 1)
+            e = launch_vote<1>(idx, ql, s);
+        else if (kr <= 2)
+            e = launch_vote<2>(idx, ql, s);
+        else if (kr <= 4)
+            e = launch_vote<4>(idx, ql, s);
+        else
+            e = launch_vote<8>(idx, ql, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
+        if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
+    } else {
+        // work counters [1] vote/emit, [2] candidate search, [3] overflow
+        // length, [4] overflow pass
+        MRPT_CUDA_TRY(cudaMemsetAsync(idx->status + 1, 0, 4 * sizeof(uint32_t), s));
+        e = launch_vote_emit(idx, ql, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k_vote_emit");
+        if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
+        if (kr <= 1)
+            e = launch_cand_knn<1>(idx, ql, s);
+        else if (kr <= 2)
+            e = launch_cand_knn<2>(idx, ql, s);
+        else if (kr <= 4)
+            e = launch_cand_knn<4>(idx, ql, s);
+        else
+            e = launch_cand_knn<8>(idx, ql, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
+        if (kr <= 1)
+            e = launch_overflow<1>(idx, ql, s);
+        else if (kr <= 2)
+            e = launch_overflow<2>(idx, ql, s);
+        else if (kr <= 4)
+            e = launch_overflow<4>(idx, ql, s);
+        else
+            e = launch_overflow<8>(idx, ql, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k_vote_search (overflow)");
+    }
     if (ql.stage_ms) {
-        MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
-        MRPT_CUDA_TRY(cudaEventSynchronize(idx->ev[2]));
+        MRPT_CUDA_TRY(cudaEventRecord(idx->ev[3], s));
+        MRPT_CUDA_TRY(cudaEventSynchronize(idx->ev[3]));
         MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[0], idx->ev[0], idx->ev[1]));
         MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[1], idx->ev[1], idx->ev[2]));
-        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[2], idx->ev[0], idx->ev[2]));
+        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[2], idx->ev[2], idx->ev[3]));
+        MRPT_CUDA_TRY(cudaEventElapsedTime(&ql.stage_ms[3], idx->ev[0], idx->ev[3]));
     }
     return MRPT_OK;
 }

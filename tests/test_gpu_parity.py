@@ -27,21 +27,21 @@ def _dens(d):
     return float(np.float32(1.0 / np.sqrt(d)))
 
 
-def _run(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False):
+def _run(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0):
     dev = torch.device("cuda:0")
     if host:
         idx = mr.mrpt_build(X, T, l, density, seed)
-        ids, dists, dbg = mr.mrpt_query_ex(idx, Q, k, v, n_trees=n_trees, debug=True)
+        ids, dists, dbg = mr.mrpt_query_ex(idx, Q, k, v, n_trees=n_trees, debug=True, path=path)
         return idx, ids, dists, dbg
     idx = mr.mrpt_build(torch.from_numpy(X).to(dev), T, l, density, seed)
     ids, dists, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).to(dev), k, v, n_trees=n_trees,
-                                       debug=True)
+                                       debug=True, path=path)
     torch.cuda.synchronize()
     return idx, ids.cpu().numpy(), dists.cpu().numpy(), {kk: vv.cpu().numpy() for kk, vv in dbg.items()}
 
 
-def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False):
-    idx, gi, gd, dbg = _run(mr, X, Q, T, l, k, v, density, seed, n_trees, host)
+def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0):
+    idx, gi, gd, dbg = _run(mr, X, Q, T, l, k, v, density, seed, n_trees, host, path)
     ref = oracle.grow_trees(X, T, l, density, seed)
     check_index_parity(idx, mr, ref)
     Tq = n_trees or T
@@ -60,23 +60,36 @@ def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False):
     return gi, gd
 
 
-def test_tiny_gaussian_mixture(mr):
+PATHS = [0, 1]  # vote/emit + candidate search, one fused kernel
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_tiny_gaussian_mixture(mr, path):
     """n=10,000, d=128, 100 clusters, T=10, l=6, v=3, k=10, seed 0."""
     X, Q = workloads.gaussian_mixture(10000, 128, 100, seed=0)
-    _full_check(mr, X, Q, 10, 6, 10, 3, _dens(128), 0)
+    _full_check(mr, X, Q, 10, 6, 10, 3, _dens(128), 0, path=path)
 
 
-def test_mnist_like_small_with_ties(mr):
+@pytest.mark.parametrize("path", PATHS)
+def test_mnist_like_small_with_ties(mr, path):
     """Sparse integer images: many projections tie exactly (often at 0), so
     the (projection, id) median order is exercised."""
     X, Q = workloads.mnist_like(4000, 40, seed=1)
-    _full_check(mr, X, Q, 16, 5, 10, 2, _dens(784), 3)
+    _full_check(mr, X, Q, 16, 5, 10, 2, _dens(784), 3, path=path)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("k", [1, 33, 100, 256])
-def test_k_values_and_padding(mr, k):
+def test_k_values_and_padding(mr, k, path):
     X, Q = workloads.gaussian_mixture(1500, 24, 30, n_centres=8, seed=4)
-    _full_check(mr, X, Q, 5, 3, k, 2, 0.3, 5)
+    _full_check(mr, X, Q, 5, 3, k, 2, 0.3, 5, path=path)
+
+
+def test_overflowing_candidate_lists(mr):
+    """|S| above the per-query list capacity (2,048): those queries are
+    answered by the fused kernel inside the same call."""
+    X, Q = workloads.gaussian_mixture(6000, 12, 20, n_centres=3, seed=12)
+    _full_check(mr, X, Q, 6, 1, 10, 1, 0.5, 3)
 
 
 def test_ragged_dimension_and_host_buffers(mr):
@@ -99,10 +112,11 @@ def test_vote_threshold_equal_to_T_and_subset_of_trees(mr):
     _full_check(mr, X, Q, 8, 4, 10, 3, _dens(32), 2, n_trees=5)
 
 
-def test_counter_chunks_beyond_shared_memory(mr):
+@pytest.mark.parametrize("path", PATHS)
+def test_counter_chunks_beyond_shared_memory(mr, path):
     """n > 65,536 ids: votes are counted in id chunks (per-tree cursors)."""
     X, Q = workloads.gaussian_mixture(140000, 8, 12, n_centres=30, seed=10)
-    _full_check(mr, X, Q, 6, 9, 10, 2, 0.5, 4)
+    _full_check(mr, X, Q, 6, 9, 10, 2, 0.5, 4, path=path)
 
 
 def test_degenerate_all_equal_points(mr):
