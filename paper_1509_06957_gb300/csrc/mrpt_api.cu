@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <new>
@@ -372,11 +373,25 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         if (bound > idx->n) bound = idx->n;
         ql.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
         if (ql.capq < 1) ql.capq = 1;
-        const size_t lb = size_t(m) * size_t(ql.capq) * 4;
-        if ((rc = idx->q_cand.ensure(lb + size_t(m) * 8, "candidate lists"))) return rc;
-        ql.cand_list = static_cast<int32_t *>(idx->q_cand.ptr);
-        ql.ncand = reinterpret_cast<int32_t *>(static_cast<char *>(idx->q_cand.ptr) + lb);
-        ql.overflow = ql.ncand + m;
+        // candidate-search work items: chunks of a list, at least 64 and at
+        // least 2k candidates each
+        ql.chunk = int32_t(std::max<int64_t>(64, ((2 * int64_t(k) + 31) / 32) * 32));
+        ql.max_items_q = (ql.capq + ql.chunk - 1) / ql.chunk;
+        // sub-buffers, each starting on a 256-byte boundary
+        auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t lb = up(size_t(m) * size_t(ql.capq) * 4);                  // lists
+        const size_t ib = up(size_t(m) * size_t(ql.max_items_q) * 8);           // items
+        const size_t pb = up(size_t(m) * size_t(ql.max_items_q) * size_t(k) * 4);  // each partial array
+        const size_t nb = up(size_t(m) * 4);                                    // ncand, overflow, done
+        if ((rc = idx->q_cand.ensure(lb + ib + 2 * pb + 3 * nb, "candidate lists"))) return rc;
+        char *base = static_cast<char *>(idx->q_cand.ptr);
+        ql.cand_list = reinterpret_cast<int32_t *>(base);
+        ql.items = reinterpret_cast<int2 *>(base + lb);
+        ql.part_d = reinterpret_cast<float *>(base + lb + ib);
+        ql.part_i = reinterpret_cast<int32_t *>(base + lb + ib + pb);
+        ql.ncand = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb);
+        ql.overflow = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb + nb);
+        ql.done = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb + 2 * nb);
     }
 
     if ((rc = launch_query(idx, ql))) return rc;

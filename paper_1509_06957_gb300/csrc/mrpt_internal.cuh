@@ -121,6 +121,12 @@ struct QueryLaunch {
     int32_t capq;
     int32_t *ncand;        // m (path 0)
     int32_t *overflow;     // m (path 0)
+    int2 *items;           // m x max_items_q (query, chunk) work items (path 0)
+    int32_t chunk;         // candidates per work item
+    int32_t max_items_q;
+    int32_t *done;         // m
+    float *part_d;         // m x max_items_q x k partial top-k lists
+    int32_t *part_i;
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);

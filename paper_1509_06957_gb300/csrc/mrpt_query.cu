@@ -252,6 +252,78 @@ __device__ __forceinline__ void rows_sq_dist(const float4 *const (&rows)[2],
     for (int r = 0; r < R; ++r) out[r] = warp_sum(acc[r][0] + acc[r][1]);
 }
 
+// ---- TMA bulk copies (global -> shared) completed on an mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// One arrival that also announces `bytes` of transactions for this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it ran out.
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 21;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Squared distance between the staged query and a row staged in shared
+// memory (consecutive float4 per lane: no bank conflicts).
+__device__ __forceinline__ float smem_row_sq_dist(const float4 *row, const float4 *q4, int nv4,
+                                                  int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int j = lane; j < nv4; j += 32) {
+        const float4 x = row[j];
+        const float4 q = q4[j];
+        const float dx = q.x - x.x, dy = q.y - x.y, dz = q.z - x.z, dw = q.w - x.w;
+        a0 = __fmaf_rn(dx, dx, a0);
+        a1 = __fmaf_rn(dy, dy, a1);
+        a0 = __fmaf_rn(dz, dz, a0);
+        a1 = __fmaf_rn(dw, dw, a1);
+    }
+    return warp_sum(a0 + a1);
+}
+
 struct VoteSearchArgs {
     const float *X;
     int64_t n;
@@ -577,6 +649,10 @@ struct VoteEmitArgs {
     int64_t *dbg_ncand;
     int32_t *dbg_cand;
     int64_t cand_cap;
+    int2 *items;           // (query, chunk) work items of k_cand_knn
+    uint32_t *n_items;
+    int32_t chunk;         // candidates per work item
+    int32_t *done;         // per query: finished work items
 };
 
 __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs a) {
@@ -637,7 +713,8 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
             }
             __syncthreads();
             // the warp's 128-id tiles, the next one loaded while the current
-            // one votes
+            // one votes; all index arithmetic is 32-bit (ids < 2^31)
+            const int32_t c0i = int32_t(c0);
             int t = warp;
             int32_t p = 0, e = 0;
             while (t < a.T_use) {
@@ -646,15 +723,18 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                 if (p < e) break;
                 t += VE_WARPS;
             }
+            const int32_t *base = a.leaf_ids + int64_t(t < a.T_use ? t : 0) * a.n;
             int32_t id[4];
+            {
+                const int rem = t < a.T_use ? e - p : 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int32_t i = p + 32 * u + lane;
-                id[u] = (t < a.T_use && i < e) ? __ldg(a.leaf_ids + int64_t(t) * a.n + i) : -1;
+                for (int u = 0; u < 4; ++u)
+                    id[u] = (32 * u + lane < rem) ? __ldg(base + p + 32 * u + lane) : -1;
             }
             while (t < a.T_use) {
                 int tn = t;
                 int32_t pn = p + 128, en = e;
+                const int32_t *bn = base;
                 if (pn >= en) {
                     if (lane == 0) cur[t] = en;
                     tn = t + VE_WARPS;
@@ -664,43 +744,50 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                         if (pn < en) break;
                         tn += VE_WARPS;
                     }
+                    bn = a.leaf_ids + int64_t(tn < a.T_use ? tn : 0) * a.n;
                 }
                 int32_t idn[4];
+                {
+                    const int rem = tn < a.T_use ? en - pn : 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int32_t i = pn + 32 * u + lane;
-                    idn[u] = (tn < a.T_use && i < en) ? __ldg(a.leaf_ids + int64_t(tn) * a.n + i) : -1;
+                    for (int u = 0; u < 4; ++u)
+                        idn[u] = (32 * u + lane < rem) ? __ldg(bn + pn + 32 * u + lane) : -1;
                 }
-                uint32_t olds[4];
+                // all four atomics first, then the emission test: the lane
+                // whose increment takes a count from v-1 to v emits the id
+                uint32_t old[4], sh[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    olds[u] = 0u;
-                    if (id[u] >= 0) {
-                        const uint32_t off = uint32_t(int64_t(id[u]) - c0);
-                        const uint32_t sh = (off & 3u) * 8u;
-                        olds[u] = atomicAdd(&cnt[off >> 2], 1u << sh) >> sh;
-                    }
+                    const uint32_t off = uint32_t(id[u] - c0i);
+                    sh[u] = (off & 3u) << 3;
+                    old[u] = id[u] >= 0 ? atomicAdd(&cnt[off >> 2], 1u << sh[u]) : 0u;
                 }
+                uint32_t emask = 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    // Algorithm 4: a point joins S when its count becomes v
-                    const bool emit = id[u] >= 0 && (olds[u] & 0xffu) == vm1;
-                    const unsigned em = __ballot_sync(0xffffffffu, emit);
-                    if (em) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&s_cnt, __popc(em));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (emit) {
-                            const int slot = base + __popc(em & lt);
-                            if (slot < a.capq) clist[slot] = id[u];
-                            if (a.dbg_cand != nullptr && slot < a.cand_cap)
-                                a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                for (int u = 0; u < 4; ++u)
+                    emask |= (id[u] >= 0 && ((old[u] >> sh[u]) & 0xffu) == vm1) ? (1u << u) : 0u;
+                if (__any_sync(0xffffffffu, emask != 0)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool emit = (emask >> u) & 1u;
+                        const unsigned em = __ballot_sync(0xffffffffu, emit);
+                        if (em) {
+                            int b0 = 0;
+                            if (lane == 0) b0 = atomicAdd(&s_cnt, __popc(em));
+                            b0 = __shfl_sync(0xffffffffu, b0, 0);
+                            if (emit) {
+                                const int slot = b0 + __popc(em & lt);
+                                if (slot < a.capq) clist[slot] = id[u];
+                                if (a.dbg_cand != nullptr && slot < a.cand_cap)
+                                    a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                            }
                         }
                     }
                 }
                 t = tn;
                 p = pn;
                 e = en;
+                base = bn;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) id[u] = idn[u];
             }
@@ -720,7 +807,16 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
             const int c = s_cnt;
             a.ncand[qi] = c;
             if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
-            if (c > a.capq) a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
+            if (c > a.capq) {
+                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
+            } else {
+                // work items of the candidate search: chunks of the list (one
+                // even when S is empty, so that the row gets its padding)
+                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
+                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
+                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
+                a.done[qi] = 0;
+            }
         }
     }
 }
@@ -730,6 +826,8 @@ constexpr int CK_WARPS = CK_THREADS / 32;
 
 struct CandKnnArgs {
     const float *X;
+    int32_t ring;          // rows staged per warp (k_cand_knn)
+    uint32_t *status;
     int32_t dpad;
     const float *Q;
     int64_t m;
@@ -741,10 +839,17 @@ struct CandKnnArgs {
     int32_t *out_ids;
     float *out_dists;
     uint32_t *work;
+    const int2 *items;
+    const uint32_t *n_items;
+    int32_t chunk;
+    int32_t max_items_q;   // chunks per query at most (partial-list slots)
+    int32_t *done;
+    float *part_d;         // partial top-k lists: m x max_items_q x k
+    int32_t *part_i;
 };
 
 template <int KR>
-__global__ void __launch_bounds__(CK_THREADS) k_cand_knn(const CandKnnArgs a) {
+__global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs a) {
     extern __shared__ __align__(16) float qsm[];  // CK_WARPS x dpad
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -796,6 +901,168 @@ __global__ void __launch_bounds__(CK_THREADS) k_cand_knn(const CandKnnArgs a) {
             }
         }
         __syncwarp();
+    }
+}
+
+// One warp per query, candidate rows streamed through a warp-private ring
+// of `ring` row slots in shared memory by bulk copies (TMA), each slot with
+// its own mbarrier: up to `ring` whole rows are in flight per warp without
+// holding them in registers, and warps never wait for one another.
+constexpr int CR_WARPS = 4;
+constexpr int CR_MAX_RING = 16;
+
+template <int KR>
+__global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    __shared__ __align__(8) uint64_t s_bar[CR_WARPS][CR_MAX_RING];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int S = a.ring;
+    const uint32_t row_bytes = uint32_t(a.dpad) * 4u;
+    unsigned char *wbase = csm + size_t(warp) * (size_t(a.dpad) * 4 + size_t(S) * row_bytes);
+    float *qv = reinterpret_cast<float *>(wbase);
+    unsigned char *ring = wbase + size_t(a.dpad) * 4;
+    uint64_t *bar = s_bar[warp];
+    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+    const unsigned char *Xb = reinterpret_cast<const unsigned char *>(a.X);
+    const int nv4 = a.dpad >> 2;
+    const int k = a.k;
+    constexpr int K2 = KR * 32;
+    if (lane == 0) {
+        for (int i = 0; i < S; ++i) mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+    }
+    __syncwarp();
+    const uint32_t n_items = *a.n_items;
+    uint32_t parity = 0;     // bit i: phase parity of slot i
+    uint32_t inflight = 0;   // bit i: slot i has a copy outstanding
+    bool failed = false;
+    int64_t staged_q = -1;
+    for (;;) {
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(a.work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= n_items) break;
+        const int2 item = a.items[w];
+        const int64_t qi = item.x;
+        const int ch = item.y;
+        const int call = a.ncand[qi];
+        const int nch = call == 0 ? 1 : (call + a.chunk - 1) / a.chunk;
+        const int lo = ch * a.chunk;
+        const int c = min(call, lo + a.chunk) - lo;  // candidates of this item
+        if (qi != staged_q) {
+            __syncwarp();
+            for (int i = lane; i < a.dpad; i += 32) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
+            staged_q = qi;
+        }
+        const int32_t *clist = a.cand + qi * int64_t(a.capq) + lo;
+        // candidate ids f in [cbase, cbase + 64) live in two registers
+        int cbase = 0;
+        int32_t ca = lane < c ? __ldg(clist + lane) : 0;
+        int32_t cb = 32 + lane < c ? __ldg(clist + 32 + lane) : 0;
+        auto id_at = [&](int f) -> int32_t {
+            const int r = f - cbase;
+            const int32_t va = __shfl_sync(0xffffffffu, ca, r & 31);
+            const int32_t vb = __shfl_sync(0xffffffffu, cb, r & 31);
+            return r < 32 ? va : vb;
+        };
+        auto issue = [&](int f, int slot) {
+            const int32_t id = id_at(f);
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bar[slot], row_bytes);
+                bulk_copy_g2s(ring + size_t(slot) * row_bytes, Xb + size_t(id) * row_bytes, row_bytes,
+                              &bar[slot]);
+            }
+            inflight |= 1u << slot;
+        };
+        const int prime = c < S ? c : S;
+        for (int f = 0; f < prime; ++f) issue(f, f);
+        __syncwarp();
+        WarpTopK<KR> top;
+        top.init();
+        int slot = 0;
+        for (int j = 0; j < c; ++j) {
+            if (j - cbase == 32) {
+                cbase += 32;
+                ca = cb;
+                cb = cbase + 32 + lane < c ? __ldg(clist + cbase + 32 + lane) : 0;
+            }
+            const int32_t id = id_at(j);
+            // warp-uniform outcome of the bounded wait
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[slot], (parity >> slot) & 1u))) {
+                failed = true;
+                break;
+            }
+            parity ^= 1u << slot;
+            inflight &= ~(1u << slot);
+            const float4 *row = reinterpret_cast<const float4 *>(ring + size_t(slot) * row_bytes);
+            const float dd = smem_row_sq_dist(row, q4, nv4, lane);
+            __syncwarp();  // every lane has read the slot
+            if (j + S < c) issue(j + S, slot);
+            top.insert(dd, id, k, lane);
+            slot = (slot + 1 == S) ? 0 : slot + 1;
+        }
+        if (failed) break;
+        bool finish = nch == 1;
+        if (!finish) {
+            // publish this chunk's list; the item that completes the query
+            // merges every chunk's list into its own
+            const int64_t pbase = (qi * a.max_items_q + ch) * int64_t(k);
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int e = r * 32 + lane;
+                if (e < k) {
+                    a.part_d[pbase + e] = top.d[r];
+                    a.part_i[pbase + e] = top.i[r];
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(a.done + qi, 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            finish = old == nch - 1;
+            if (finish) {
+                __threadfence();
+                for (int ch2 = 0; ch2 < nch; ++ch2) {
+                    if (ch2 == ch) continue;
+                    const int64_t b2 = (qi * a.max_items_q + ch2) * int64_t(k);
+                    for (int e0 = 0; e0 < k; e0 += 32) {
+                        float pd = INFINITY;
+                        int32_t pi = SENTINEL_ID;
+                        if (e0 + lane < k) {
+                            pd = __ldcg(a.part_d + b2 + e0 + lane);
+                            pi = __ldcg(a.part_i + b2 + e0 + lane);
+                        }
+                        const int cnt = min(32, k - e0);
+                        for (int u = 0; u < cnt; ++u) {
+                            const float ud = __shfl_sync(0xffffffffu, pd, u);
+                            const int32_t ui = __shfl_sync(0xffffffffu, pi, u);
+                            top.insert(ud, ui, k, lane);
+                        }
+                    }
+                }
+            }
+        }
+        if (finish) {
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int e = r * 32 + lane;
+                if (e < k) {
+                    const bool real = top.i[r] != SENTINEL_ID;
+                    a.out_ids[qi * k + e] = real ? top.i[r] : -1;
+                    a.out_dists[qi * k + e] = real ? sqrtf(top.d[r]) : INFINITY;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (failed && lane == 0) {
+        atomicOr(a.status, STATUS_TIMEOUT);
+        // let copies still in flight land before the warp exits (bounded)
+        for (int i = 0; i < S; ++i)
+            if ((inflight >> i) & 1u) mbar_wait(&bar[i], (parity >> i) & 1u);
     }
 }
 
@@ -943,6 +1210,10 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.n_overflow = idx->status + 3;
     a.work = idx->status + 1;
     a.cnt_words = cnt_words;
+    a.items = ql.items;
+    a.n_items = idx->status + 5;
+    a.chunk = ql.chunk;
+    a.done = ql.done;
     a.dbg_votes = ql.votes;
     a.dbg_ncand = ql.n_cand;
     a.dbg_cand = ql.cand;
@@ -953,17 +1224,10 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
 
 template <int KR>
 cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const size_t smem = size_t(CK_WARPS) * size_t(idx->dpad) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_cand_knn<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR>, CK_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(
-        1, std::min<int64_t>((ql.m + CK_WARPS - 1) / CK_WARPS, int64_t(sms) * std::max(per_sm, 1)));
+    const size_t row_bytes = size_t(idx->dpad) * 4;
+    // ring of rows per warp: about 12 KB of rows, 2..16 slots
+    int ring = int(std::min<size_t>(CR_MAX_RING, std::max<size_t>(2, (12 * 1024) / row_bytes)));
+    const size_t per_warp = row_bytes + size_t(ring) * row_bytes;
     CandKnnArgs a{};
     a.X = idx->X;
     a.dpad = idx->dpad;
@@ -977,7 +1241,40 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.out_ids = ql.out_ids;
     a.out_dists = ql.out_dists;
     a.work = idx->status + 2;
-    k_cand_knn<KR><<<unsigned(blocks), CK_THREADS, smem, s>>>(a);
+    a.ring = ring;
+    a.status = idx->status;
+    a.items = ql.items;
+    a.n_items = idx->status + 5;
+    a.chunk = ql.chunk;
+    a.max_items_q = ql.max_items_q;
+    a.done = ql.done;
+    a.part_d = ql.part_d;
+    a.part_i = ql.part_i;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e != cudaSuccess) return e;
+    if (CR_WARPS * per_warp <= 200 * 1024) {
+        const size_t smem = CR_WARPS * per_warp;
+        e = cudaFuncSetAttribute(k_cand_knn<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR>, CR_WARPS * 32, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::max<int64_t>(
+            1, std::min<int64_t>((ql.m + CR_WARPS - 1) / CR_WARPS, int64_t(sms) * std::max(per_sm, 1)));
+        k_cand_knn<KR><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    // rows too long to stage: register path
+    const size_t smem = size_t(CK_WARPS) * size_t(idx->dpad) * 4;
+    e = cudaFuncSetAttribute(k_cand_knn_regs<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn_regs<KR>, CK_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(
+        1, std::min<int64_t>((ql.m + CK_WARPS - 1) / CK_WARPS, int64_t(sms) * std::max(per_sm, 1)));
+    k_cand_knn_regs<KR><<<unsigned(blocks), CK_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1028,8 +1325,8 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
     } else {
         // work counters [1] vote/emit, [2] candidate search, [3] overflow
-        // length, [4] overflow pass
-        MRPT_CUDA_TRY(cudaMemsetAsync(idx->status + 1, 0, 4 * sizeof(uint32_t), s));
+        // length, [4] overflow pass, [5] candidate-search work items
+        MRPT_CUDA_TRY(cudaMemsetAsync(idx->status + 1, 0, 5 * sizeof(uint32_t), s));
         e = launch_vote_emit(idx, ql, s);
         if (e != cudaSuccess) return cuda_fail(e, "k_vote_emit");
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
