@@ -224,9 +224,11 @@ def run_gpu(args):
     dists = torch.empty((m, k), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def query(T_use, v, stage=None):
+    mr.mrpt_add_lowp(index)
+
+    def query(T_use, v, stage=None, prec=0, margin=0):
         mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, out_ids=ids, out_dists=dists,
-                         stage_ms=stage, path=args.path)
+                         stage_ms=stage, path=args.path, precision=prec, margin=margin)
 
     # ---- sweep (T, v): fastest with recall >= target (tie-aware), unless
     # the operating point is given
@@ -234,16 +236,23 @@ def run_gpu(args):
     stage = np.zeros(4, np.float32)
     grid = [(args.T, args.v)] if args.T and args.v else \
         [(T_, v_) for T_ in W["T_grid"] for v_ in W["v_grid"] if v_ <= T_]
+    precs = [(0, 0)] if args.path == 1 or args.precision == "fp32" else \
+        ([(1, m_) for m_ in (0, 8, 32)] if args.precision == "bf16" else
+         [(0, 0)] + [(1, m_) for m_ in (0, 8, 32)])
     for T_use, v in grid:
-        query(T_use, v)  # warm
-        flush.zero_()
-        query(T_use, v, stage)
-        rs, rt = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
-        sweep.append(dict(T=T_use, v=v, ms=float(stage[3]), recall=round(rt, 4),
-                          recall_strict=round(rs, 4)))
+        for prec, margin in precs:
+            query(T_use, v, prec=prec, margin=margin)  # warm
+            flush.zero_()
+            query(T_use, v, stage, prec=prec, margin=margin)
+            rs, rt = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
+            sweep.append(dict(T=T_use, v=v, precision="bf16" if prec else "fp32", margin=margin,
+                              ms=float(stage[3]), recall=round(rt, 4), recall_strict=round(rs, 4)))
     ok = [s for s in sweep if s["recall"] >= W["target_recall"]]
     best = min(ok, key=lambda s: s["ms"]) if ok else max(sweep, key=lambda s: s["recall"])
     T_use, v = best["T"], best["v"]
+    prec, margin = (1 if best["precision"] == "bf16" else 0), best["margin"]
+    ok32 = [s for s in ok if s["precision"] == "fp32"]
+    best32 = min(ok32, key=lambda s: s["ms"]) if ok32 else None
 
     # ---- mean |S| at the operating point (untimed debug pass)
     _, _, dbg = mr.mrpt_query_ex(index, Q[:2000], k, v, n_trees=T_use, debug=True, cand_cap=1)
@@ -252,7 +261,7 @@ def run_gpu(args):
 
     # ---- timed steps (device-resident inputs)
     for _ in range(args.warmup):
-        query(T_use, v)
+        query(T_use, v, prec=prec, margin=margin)
     torch.cuda.synchronize()
     per_step, vote_ms, route_ms, search_ms = [], [], [], []
     if world > 1:
@@ -261,7 +270,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
-            query(T_use, v, stage)
+            query(T_use, v, stage, prec=prec, margin=margin)
             route_ms.append(float(stage[0]))
             vote_ms.append(float(stage[1]))
             search_ms.append(float(stage[2]))
@@ -282,14 +291,14 @@ def run_gpu(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch)
+        e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec, margin)
 
     # ---- rooflines: voting (leaf ids, L2-resident) and candidate search
     # (candidate rows); "roofline" reports the kernel that takes longer
     peak, peak_kind = load_peaks()
     L = 1 << l
     leaf_bytes = T_use * math.ceil(n / L) * 4
-    row_bytes = mean_S * d * 4
+    row_bytes = mean_S * d * (2 if prec else 4) + (min(k + margin, mean_S) * d * 4 if prec else 0)
     vote_avg = statistics.mean(vote_ms)
     search_avg = statistics.mean(search_ms)
     if args.path == 1:
@@ -327,9 +336,13 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 rows, f32 accumulate + f32 re-rank" if prec else "f32",
+            "data": "synthetic",
             "config": {"workload": W["name"], "n": n, "d": d, "queries_per_step": m, "k": k,
                        "depth": l, "T": T_use, "v": v, "density": "1/sqrt(d)",
+                       "precision": "bf16" if prec else "fp32", "rerank_margin": margin,
+                       "fp32_best": best32,
                        "recall_at_10": round(recall_ta, 4),
                        "recall_at_10_strict": round(recall_strict, 4),
                        "mean_candidates": round(mean_S, 1), "build_s_T200": round(build_s, 3),
@@ -353,20 +366,23 @@ def run_gpu(args):
     return out
 
 
-def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch):
+def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec=0, margin=0):
     """The same metric through the public call with pinned host buffers:
     every step copies the queries in and the results out."""
     m, d = Q.shape
     Qh = Q.cpu().pin_memory().numpy()
     ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory().numpy()
     dists_h = torch.empty((m, k), dtype=torch.float32).pin_memory().numpy()
-    mr.mrpt_query(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h)
+    def call():
+        mr.mrpt_query_ex(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h,
+                         precision=prec, margin=margin)
+    call()
     el = 0.0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mr.mrpt_query(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h)
+        call()
         el += time.perf_counter() - t0
     if world > 1:
         import torch.distributed as dist
@@ -472,6 +488,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto",
+                    help="candidate-distance precision (auto: the faster at the recall target)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1],
                     help="0: vote/emit + candidate search kernels, 1: one fused kernel")
     ap.add_argument("--T", type=int, default=0, help="fix the number of trees (with --v)")

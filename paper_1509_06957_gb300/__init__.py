@@ -50,8 +50,10 @@ EXPORT = {
 ABI_SYMBOLS = (
     "mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
-    "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc",
+    "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
 )
+MRPT_PREC_FP32 = 0
+MRPT_PREC_BF16 = 1
 MRPT_NOALLOC_MAX_LEAF_ENTRIES = 1048512
 
 
@@ -65,6 +67,10 @@ class QueryOpts(ctypes.Structure):
     _fields_ = [
         ("n_trees", ctypes.c_int32),
         ("path", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("margin", ctypes.c_int32),
+        ("chunk", ctypes.c_int32),
+        ("ring", ctypes.c_int32),
         ("proj", ctypes.c_void_p),
         ("leaf", ctypes.c_void_p),
         ("votes", ctypes.c_void_p),
@@ -133,6 +139,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_export.argtypes = [vp, i32, vp, i64]
         lib.mrpt_debug_fail_alloc_after.restype = ctypes.c_int
         lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
+        lib.mrpt_add_lowp.restype = ctypes.c_int
+        lib.mrpt_add_lowp.argtypes = [vp, i32]
         lib.mrpt_query_noalloc.restype = ctypes.c_int
         lib.mrpt_query_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp]
         _lib = lib
@@ -248,6 +256,11 @@ def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0) -> Ind
     return Index(h)
 
 
+def mrpt_add_lowp(index: Index, precision: int = MRPT_PREC_BF16) -> None:
+    """Add a bfloat16 copy of the data for reduced-precision distances."""
+    _check(load_library().mrpt_add_lowp(index.handle, int(precision)))
+
+
 def mrpt_free(index: Index) -> None:
     index.close()
 
@@ -271,14 +284,17 @@ def mrpt_info(index: Index) -> IndexInfo:
 
 def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
                   out_dists=None, debug: bool = False, cand_cap: int | None = None,
-                  stage_ms=None, path: int = 0):
+                  stage_ms=None, path: int = 0, precision: int = 0, margin: int = 0,
+                  chunk: int = 0, ring: int = 0):
     """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
     tensors for a CUDA tensor, numpy arrays for host input) unless given.
     With ``debug`` also returns a dict of the internals: proj, leaf, votes,
     n_cand and cand (members of S, row padded).  ``stage_ms`` (a float32
     numpy array of 4) receives the routing, voting, candidate-search and
     total device times of this call in ms.  ``path`` 0 runs the vote/emit
-    and candidate-search kernels, 1 the fused kernel."""
+    and candidate-search kernels, 1 the fused kernel.  ``precision``
+    MRPT_PREC_BF16 computes candidate distances from the bfloat16 copy
+    (mrpt_add_lowp) and re-ranks the k + ``margin`` nearest in float32."""
     lib = load_library()
     Q = _as_f32(Q)
     m = Q.shape[0]
@@ -292,6 +308,10 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
     opts = QueryOpts()
     opts.n_trees = int(n_trees)
     opts.path = int(path)
+    opts.precision = int(precision)
+    opts.margin = int(margin)
+    opts.chunk = int(chunk)
+    opts.ring = int(ring)
     if stage_ms is not None:
         assert stage_ms.dtype == np.float32 and stage_ms.size >= 4
         opts.stage_ms = stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))

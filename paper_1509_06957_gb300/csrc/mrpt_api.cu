@@ -90,6 +90,7 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->split);
     cudaFree(idx->leaf_off);
     cudaFree(idx->leaf_ids);
+    cudaFree(idx->Xb);
     cudaFree(idx->status);
     for (cudaEvent_t &ev : idx->ev)
         if (ev) cudaEventDestroy(ev);
@@ -284,9 +285,30 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
                   std::to_string(MRPT_MAX_K) + ", 1 <= v <= n_trees <= T)");
         return MRPT_ERR_INVALID_ARG;
     }
+    if (opts && (opts->chunk < 0 || opts->ring < 0)) {
+        set_error("mrpt_query: chunk and ring must be >= 0");
+        return MRPT_ERR_INVALID_ARG;
+    }
     if (opts && opts->cand && opts->cand_cap < 0) {
         set_error("mrpt_query: cand_cap < 0");
         return MRPT_ERR_INVALID_ARG;
+    }
+    const int32_t precision = opts ? opts->precision : MRPT_PREC_FP32;
+    const int32_t margin = (opts && precision == MRPT_PREC_BF16) ? opts->margin : 0;
+    if (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16) {
+        set_error("mrpt_query: unknown precision");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (precision == MRPT_PREC_BF16) {
+        if (!idx->Xb) {
+            set_error("mrpt_query: bfloat16 distances need mrpt_add_lowp(idx, MRPT_PREC_BF16) first");
+            return MRPT_ERR_INVALID_ARG;
+        }
+        if (opts->path != 0 || margin < 0 || k + margin > MRPT_MAX_K) {
+            set_error("mrpt_query: bfloat16 distances need path 0 and 0 <= margin, k + margin <= " +
+                      std::to_string(MRPT_MAX_K));
+            return MRPT_ERR_INVALID_ARG;
+        }
     }
     if (m == 0) return MRPT_OK;
     cudaStream_t s = idx->stream;
@@ -365,7 +387,10 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         ql.leaf = static_cast<int32_t *>(idx->q_leaf.ptr);
     }
     ql.path = opts ? opts->path : 0;
+    ql.precision = precision;
+    ql.margin = margin;
     if (ql.path == 0) {
+        const int64_t ks = int64_t(k) + margin;  // list length kept per chunk
         // |S| <= T ceil(n / 2^l) / v (Sec. III-B: every member of S holds at
         // least v of the T ceil(n / 2^l) votes), and |S| <= n
         const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
@@ -373,15 +398,17 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         if (bound > idx->n) bound = idx->n;
         ql.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
         if (ql.capq < 1) ql.capq = 1;
-        // candidate-search work items: chunks of a list, at least 64 and at
-        // least 2k candidates each
-        ql.chunk = int32_t(std::max<int64_t>(64, ((2 * int64_t(k) + 31) / 32) * 32));
+        // candidate-search work items: chunks of a list, at least 128 and at
+        // least 2(k + margin) candidates each
+        ql.chunk = int32_t(std::max<int64_t>(precision == MRPT_PREC_BF16 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
+        if (opts && opts->chunk > 0) ql.chunk = int32_t(std::max<int64_t>(opts->chunk, ks));
+        ql.ring = (opts && opts->ring > 0) ? std::min<int32_t>(std::max<int32_t>(opts->ring, 2), 16) : 0;
         ql.max_items_q = (ql.capq + ql.chunk - 1) / ql.chunk;
         // sub-buffers, each starting on a 256-byte boundary
         auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
         const size_t lb = up(size_t(m) * size_t(ql.capq) * 4);                  // lists
         const size_t ib = up(size_t(m) * size_t(ql.max_items_q) * 8);           // items
-        const size_t pb = up(size_t(m) * size_t(ql.max_items_q) * size_t(k) * 4);  // each partial array
+        const size_t pb = up(size_t(m) * size_t(ql.max_items_q) * size_t(ks) * 4);  // each partial array
         const size_t nb = up(size_t(m) * 4);                                    // ncand, overflow, done
         if ((rc = idx->q_cand.ensure(lb + ib + 2 * pb + 3 * nb, "candidate lists"))) return rc;
         char *base = static_cast<char *>(idx->q_cand.ptr);
@@ -405,6 +432,15 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
                                           dbg[i].bytes, cudaMemcpyDeviceToHost, s));
     if (any_host) return mrpt_sync(idx);
     return MRPT_OK;
+}
+
+int mrpt_add_lowp(mrpt_index *idx, int32_t precision) {
+    clear_error();
+    if (!idx || precision != MRPT_PREC_BF16) {
+        set_error("mrpt_add_lowp: need an index and precision MRPT_PREC_BF16");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    return make_bf16_copy(idx);
 }
 
 int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v, int32_t *out_ids,

@@ -61,6 +61,8 @@ struct mrpt_index {
     cudaStream_t stream = nullptr;
 
     float *X = nullptr;          // n x dpad, zero padded
+    uint16_t *Xb = nullptr;      // optional bfloat16 copy of X (same stride)
+    bool bf16_exact = false;     // every value of X is exactly representable in bfloat16
     int32_t *col_off = nullptr;  // T*l + 1
     int32_t *dim = nullptr;      // nnz
     float *val = nullptr;        // nnz
@@ -127,6 +129,9 @@ struct QueryLaunch {
     int32_t *done;         // m
     float *part_d;         // m x max_items_q x k partial top-k lists
     int32_t *part_i;
+    int32_t precision;     // 0 float32 rows, 1 bfloat16 rows + float32 re-rank
+    int32_t margin;        // survivors beyond k kept for the re-rank
+    int32_t ring;          // candidate rows staged per search warp (0 = auto)
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);
@@ -134,5 +139,8 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql);
 // launch_query with caller-supplied scratch: ql.leaf holds the m x n_trees
 // leaf-of-query table and `work` the work counter.
 int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *work);
+
+// Fills idx->Xb with X rounded to bfloat16 (allocating it on first use).
+int make_bf16_copy(mrpt_index *idx);
 
 }  // namespace mrpt

@@ -13,6 +13,7 @@
 //                   float32 squared distance with 128-bit loads and keeps a
 //                   per-warp sorted top-k in registers; the warps' lists are
 //                   merged by rank (knn(q, k, S) of Algorithm 4).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -322,6 +323,91 @@ __device__ __forceinline__ float smem_row_sq_dist(const float4 *row, const float
         a1 = __fmaf_rn(dw, dw, a1);
     }
     return warp_sum(a0 + a1);
+}
+
+// The same for a bfloat16 row: 8 components per 16-byte load, widened to
+// float exactly, differences and accumulation in float32.
+__device__ __forceinline__ float smem_row_sq_dist_bf16(const uint4 *row, const float4 *q4, int nv8,
+                                                       int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int j = lane; j < nv8; j += 32) {
+        const uint4 raw = row[j];
+        const float4 qa = q4[2 * j];
+        const float4 qb = q4[2 * j + 1];
+        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+        const float qs[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float lo = __uint_as_float(w[h] << 16);
+            const float hi = __uint_as_float(w[h] & 0xffff0000u);
+            const float d0 = qs[2 * h] - lo, d1 = qs[2 * h + 1] - hi;
+            a0 = __fmaf_rn(d0, d0, a0);
+            a1 = __fmaf_rn(d1, d1, a1);
+        }
+    }
+    return warp_sum(a0 + a1);
+}
+
+// Two staged rows against the staged query at once: one query load feeds
+// both rows and the two warp reductions interleave.  ROW is float4 (float32
+// rows) or uint2 (four bfloat16 values); either way step j covers query
+// components 4j .. 4j+3, so every lane reads consecutive 16-byte query
+// chunks (no bank conflicts).
+template <typename ROW>
+__device__ __forceinline__ float4 row_chunk(const ROW &x);
+
+template <>
+__device__ __forceinline__ float4 row_chunk<float4>(const float4 &x) {
+    return x;
+}
+
+template <>
+__device__ __forceinline__ float4 row_chunk<uint2>(const uint2 &x) {
+    return make_float4(__uint_as_float(x.x << 16), __uint_as_float(x.x & 0xffff0000u),
+                       __uint_as_float(x.y << 16), __uint_as_float(x.y & 0xffff0000u));
+}
+
+template <typename ROW>
+__device__ __forceinline__ void smem_rows2_sq_dist(const ROW *r0, const ROW *r1, const float4 *q4,
+                                                   int nv4, int lane, float &d0, float &d1) {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll 2
+    for (int j = lane; j < nv4; j += 32) {
+        const float4 q = q4[j];
+        const float4 x = row_chunk<ROW>(r0[j]);
+        const float4 y = row_chunk<ROW>(r1[j]);
+        float t;
+        t = q.x - x.x; a0 = __fmaf_rn(t, t, a0);
+        t = q.y - x.y; a1 = __fmaf_rn(t, t, a1);
+        t = q.z - x.z; a0 = __fmaf_rn(t, t, a0);
+        t = q.w - x.w; a1 = __fmaf_rn(t, t, a1);
+        t = q.x - y.x; b0 = __fmaf_rn(t, t, b0);
+        t = q.y - y.y; b1 = __fmaf_rn(t, t, b1);
+        t = q.z - y.z; b0 = __fmaf_rn(t, t, b0);
+        t = q.w - y.w; b1 = __fmaf_rn(t, t, b1);
+    }
+    float sa = a0 + a1, sb = b0 + b1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    d0 = sa;
+    d1 = sb;
+}
+
+// float32 rows -> bfloat16 copy (round to nearest even), same row stride;
+// *lossy is set when some value does not survive the rounding.
+__global__ void k_to_bf16(const float *__restrict__ X, __nv_bfloat16 *__restrict__ Y, int64_t count,
+                          uint32_t *__restrict__ lossy) {
+    bool diff = false;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const __nv_bfloat16 y = __float2bfloat16_rn(X[i]);
+        Y[i] = y;
+        diff |= __bfloat162float(y) != X[i];
+    }
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(lossy, 1u);
 }
 
 struct VoteSearchArgs {
@@ -826,6 +912,9 @@ constexpr int CK_WARPS = CK_THREADS / 32;
 
 struct CandKnnArgs {
     const float *X;
+    const void *rows;      // rows the distances are computed from (X or its bf16 copy)
+    int32_t kfinal;        // neighbours returned (k); a.k holds k + margin when re-ranking
+    int32_t rerank;        // re-rank the survivors with float32 rows
     int32_t ring;          // rows staged per warp (k_cand_knn)
     uint32_t *status;
     int32_t dpad;
@@ -911,23 +1000,23 @@ __global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs 
 constexpr int CR_WARPS = 4;
 constexpr int CR_MAX_RING = 16;
 
-template <int KR>
+template <int KR, bool BF16>
 __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a) {
     extern __shared__ __align__(16) unsigned char csm[];
     __shared__ __align__(8) uint64_t s_bar[CR_WARPS][CR_MAX_RING];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int S = a.ring;
-    const uint32_t row_bytes = uint32_t(a.dpad) * 4u;
+    const uint32_t row_bytes = uint32_t(a.dpad) * (BF16 ? 2u : 4u);
     unsigned char *wbase = csm + size_t(warp) * (size_t(a.dpad) * 4 + size_t(S) * row_bytes);
     float *qv = reinterpret_cast<float *>(wbase);
     unsigned char *ring = wbase + size_t(a.dpad) * 4;
     uint64_t *bar = s_bar[warp];
     const float4 *q4 = reinterpret_cast<const float4 *>(qv);
-    const unsigned char *Xb = reinterpret_cast<const unsigned char *>(a.X);
+    const unsigned char *Xb = reinterpret_cast<const unsigned char *>(a.rows);
+    const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
     const int nv4 = a.dpad >> 2;
     const int k = a.k;
-    constexpr int K2 = KR * 32;
     if (lane == 0) {
         for (int i = 0; i < S; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -935,25 +1024,40 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a)
     }
     __syncwarp();
     const uint32_t n_items = *a.n_items;
+    const bool qvec = (a.d & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Q) & 15) == 0;
     uint32_t parity = 0;     // bit i: phase parity of slot i
     uint32_t inflight = 0;   // bit i: slot i has a copy outstanding
     bool failed = false;
     int64_t staged_q = -1;
+    // the next work item is claimed (and its record read) one item ahead
+    uint32_t w = 0;
+    if (lane == 0) w = atomicAdd(a.work, 1u);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    int2 item = make_int2(0, 0);
+    int call = 0;
+    if (w < n_items) {
+        item = a.items[w];
+        call = a.ncand[item.x];
+    }
     for (;;) {
-        uint32_t w = 0;
-        if (lane == 0) w = atomicAdd(a.work, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= n_items) break;
-        const int2 item = a.items[w];
         const int64_t qi = item.x;
         const int ch = item.y;
-        const int call = a.ncand[qi];
+        uint32_t w_next = 0;
+        if (lane == 0) w_next = atomicAdd(a.work, 1u);
         const int nch = call == 0 ? 1 : (call + a.chunk - 1) / a.chunk;
         const int lo = ch * a.chunk;
         const int c = min(call, lo + a.chunk) - lo;  // candidates of this item
         if (qi != staged_q) {
             __syncwarp();
-            for (int i = lane; i < a.dpad; i += 32) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
+            if (qvec) {
+                const float4 *src = reinterpret_cast<const float4 *>(a.Q + qi * a.d);
+                float4 *dst = reinterpret_cast<float4 *>(qv);
+                for (int i = lane; i < (a.dpad >> 2); i += 32)
+                    dst[i] = 4 * i < a.d ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int i = lane; i < a.dpad; i += 32) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
+            }
             staged_q = qi;
         }
         const int32_t *clist = a.cand + qi * int64_t(a.capq) + lo;
@@ -982,26 +1086,44 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a)
         WarpTopK<KR> top;
         top.init();
         int slot = 0;
-        for (int j = 0; j < c; ++j) {
-            if (j - cbase == 32) {
+        for (int j = 0; j < c; j += 2) {
+            if (j - cbase >= 32) {
                 cbase += 32;
                 ca = cb;
                 cb = cbase + 32 + lane < c ? __ldg(clist + cbase + 32 + lane) : 0;
             }
-            const int32_t id = id_at(j);
-            // warp-uniform outcome of the bounded wait
-            if (!__all_sync(0xffffffffu, mbar_wait(&bar[slot], (parity >> slot) & 1u))) {
+            const bool two = j + 1 < c;
+            const int slot1 = (slot + 1 == S) ? 0 : slot + 1;
+            const int32_t id0 = id_at(j);
+            const int32_t id1 = two ? id_at(j + 1) : id0;
+            // warp-uniform outcome of the bounded waits
+            bool ok = mbar_wait(&bar[slot], (parity >> slot) & 1u);
+            if (two) ok = mbar_wait(&bar[slot1], (parity >> slot1) & 1u) && ok;
+            if (!__all_sync(0xffffffffu, ok)) {
                 failed = true;
                 break;
             }
             parity ^= 1u << slot;
             inflight &= ~(1u << slot);
-            const float4 *row = reinterpret_cast<const float4 *>(ring + size_t(slot) * row_bytes);
-            const float dd = smem_row_sq_dist(row, q4, nv4, lane);
-            __syncwarp();  // every lane has read the slot
+            if (two) {
+                parity ^= 1u << slot1;
+                inflight &= ~(1u << slot1);
+            }
+            float dd0, dd1;
+            if (BF16)
+                smem_rows2_sq_dist<uint2>(reinterpret_cast<const uint2 *>(ring + size_t(slot) * row_bytes),
+                                          reinterpret_cast<const uint2 *>(ring + size_t(two ? slot1 : slot) * row_bytes),
+                                          q4, nv4, lane, dd0, dd1);
+            else
+                smem_rows2_sq_dist<float4>(reinterpret_cast<const float4 *>(ring + size_t(slot) * row_bytes),
+                                           reinterpret_cast<const float4 *>(ring + size_t(two ? slot1 : slot) * row_bytes),
+                                           q4, nv4, lane, dd0, dd1);
+            __syncwarp();  // every lane has read both slots
             if (j + S < c) issue(j + S, slot);
-            top.insert(dd, id, k, lane);
-            slot = (slot + 1 == S) ? 0 : slot + 1;
+            if (two && j + 1 + S < c) issue(j + 1 + S, slot1);
+            top.insert(dd0, id0, k, lane);
+            if (two) top.insert(dd1, id1, k, lane);
+            slot = two ? ((slot1 + 1 == S) ? 0 : slot1 + 1) : slot1;
         }
         if (failed) break;
         bool finish = nch == 1;
@@ -1045,18 +1167,78 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a)
                 }
             }
         }
+        if (finish && BF16 && a.rerank) {
+            // re-rank: exact float32 distances of the k + margin survivors,
+            // whose float32 rows stream through the ring two bfloat16 slots
+            // at a time; keep the k smallest
+            const int S2 = S / 2;
+            const uint32_t frow = row_bytes * 2u;
+            const unsigned char *Xf = reinterpret_cast<const unsigned char *>(a.X);
+            auto sid = [&](int f) -> int32_t {
+                int32_t v = SENTINEL_ID;
+#pragma unroll
+                for (int rr = 0; rr < KR; ++rr) {
+                    const int32_t t2 = __shfl_sync(0xffffffffu, top.i[rr], f & 31);
+                    if (rr == (f >> 5)) v = t2;
+                }
+                return v;
+            };
+            int nsurv = 0;
+#pragma unroll
+            for (int rr = 0; rr < KR; ++rr)
+                nsurv += __popc(__ballot_sync(0xffffffffu, rr * 32 + lane < k && top.i[rr] != SENTINEL_ID));
+            auto issue2 = [&](int f, int ss) {
+                const int32_t id2 = sid(f);
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&bar[2 * ss], frow);
+                    bulk_copy_g2s(ring + size_t(2 * ss) * row_bytes, Xf + size_t(id2) * frow, frow,
+                                  &bar[2 * ss]);
+                }
+                inflight |= 1u << (2 * ss);
+            };
+            const int prime2 = nsurv < S2 ? nsurv : S2;
+            for (int f = 0; f < prime2; ++f) issue2(f, f);
+            __syncwarp();
+            WarpTopK<KR> fin;
+            fin.init();
+            int ss = 0;
+            for (int f = 0; f < nsurv; ++f) {
+                const int32_t id2 = sid(f);
+                const int bslot = 2 * ss;
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar[bslot], (parity >> bslot) & 1u))) {
+                    failed = true;
+                    break;
+                }
+                parity ^= 1u << bslot;
+                inflight &= ~(1u << bslot);
+                const float ed = smem_row_sq_dist(
+                    reinterpret_cast<const float4 *>(ring + size_t(bslot) * row_bytes), q4, nv4, lane);
+                __syncwarp();
+                if (f + S2 < nsurv) issue2(f + S2, ss);
+                fin.insert(ed, id2, a.kfinal, lane);
+                ss = (ss + 1 == S2) ? 0 : ss + 1;
+            }
+            if (failed) break;
+            top = fin;
+        }
         if (finish) {
+            const int kf = a.kfinal;
 #pragma unroll
             for (int r = 0; r < KR; ++r) {
                 const int e = r * 32 + lane;
-                if (e < k) {
+                if (e < kf) {
                     const bool real = top.i[r] != SENTINEL_ID;
-                    a.out_ids[qi * k + e] = real ? top.i[r] : -1;
-                    a.out_dists[qi * k + e] = real ? sqrtf(top.d[r]) : INFINITY;
+                    a.out_ids[qi * kf + e] = real ? top.i[r] : -1;
+                    a.out_dists[qi * kf + e] = real ? sqrtf(top.d[r]) : INFINITY;
                 }
             }
         }
         __syncwarp();
+        w = __shfl_sync(0xffffffffu, w_next, 0);
+        if (w < n_items) {
+            item = a.items[w];
+            call = a.ncand[item.x];
+        }
     }
     if (failed && lane == 0) {
         atomicOr(a.status, STATUS_TIMEOUT);
@@ -1222,14 +1404,18 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     return cudaGetLastError();
 }
 
-template <int KR>
+template <int KR, bool BF16>
 cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const size_t row_bytes = size_t(idx->dpad) * 4;
-    // ring of rows per warp: about 12 KB of rows, 2..16 slots
-    int ring = int(std::min<size_t>(CR_MAX_RING, std::max<size_t>(2, (12 * 1024) / row_bytes)));
-    const size_t per_warp = row_bytes + size_t(ring) * row_bytes;
+    const size_t row_bytes = size_t(idx->dpad) * (BF16 ? 2 : 4);
+    // rows staged per warp: two (one pair in flight) by default -- the
+    // kernel hides latency with resident warps rather than ring depth, so
+    // the smallest ring (most warps per SM) measured fastest
+    int ring = ql.ring > 0 ? ql.ring : 2;
+    const size_t per_warp = size_t(idx->dpad) * 4 + size_t(ring) * row_bytes;
     CandKnnArgs a{};
     a.X = idx->X;
+    a.rows = BF16 ? static_cast<const void *>(idx->Xb) : static_cast<const void *>(idx->X);
+    a.kfinal = ql.k;
     a.dpad = idx->dpad;
     a.Q = ql.Q;
     a.m = ql.m;
@@ -1237,7 +1423,10 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.cand = ql.cand_list;
     a.capq = ql.capq;
     a.ncand = ql.ncand;
-    a.k = ql.k;
+    // a lossless bfloat16 copy gives float32 distances up to summation
+    // order: no survivors beyond k and no re-rank are needed
+    a.rerank = (BF16 && !idx->bf16_exact) ? 1 : 0;
+    a.k = ql.k + (a.rerank ? ql.margin : 0);
     a.out_ids = ql.out_ids;
     a.out_dists = ql.out_dists;
     a.work = idx->status + 2;
@@ -1253,19 +1442,19 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
     if (e != cudaSuccess) return e;
-    if (CR_WARPS * per_warp <= 200 * 1024) {
+    if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
-        e = cudaFuncSetAttribute(k_cand_knn<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        e = cudaFuncSetAttribute(k_cand_knn<KR, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR>, CR_WARPS * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR, BF16>, CR_WARPS * 32, smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((ql.m + CR_WARPS - 1) / CR_WARPS, int64_t(sms) * std::max(per_sm, 1)));
-        k_cand_knn<KR><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
+        k_cand_knn<KR, BF16><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
         return cudaGetLastError();
     }
-    // rows too long to stage: register path
+    // float32 rows too long to stage: register path
     const size_t smem = size_t(CK_WARPS) * size_t(idx->dpad) * 4;
     e = cudaFuncSetAttribute(k_cand_knn_regs<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -1330,14 +1519,26 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
         e = launch_vote_emit(idx, ql, s);
         if (e != cudaSuccess) return cuda_fail(e, "k_vote_emit");
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
-        if (kr <= 1)
-            e = launch_cand_knn<1>(idx, ql, s);
-        else if (kr <= 2)
-            e = launch_cand_knn<2>(idx, ql, s);
-        else if (kr <= 4)
-            e = launch_cand_knn<4>(idx, ql, s);
-        else
-            e = launch_cand_knn<8>(idx, ql, s);
+        if (ql.precision == 1) {
+            // survivors kept for the re-rank (none beyond k when it is skipped)
+            const int krs = (ql.k + (idx->bf16_exact ? 0 : ql.margin) + 31) / 32;
+            if (krs <= 1)
+                e = launch_cand_knn<1, true>(idx, ql, s);
+            else if (krs <= 2)
+                e = launch_cand_knn<2, true>(idx, ql, s);
+            else if (krs <= 4)
+                e = launch_cand_knn<4, true>(idx, ql, s);
+            else
+                e = launch_cand_knn<8, true>(idx, ql, s);
+        } else if (kr <= 1) {
+            e = launch_cand_knn<1, false>(idx, ql, s);
+        } else if (kr <= 2) {
+            e = launch_cand_knn<2, false>(idx, ql, s);
+        } else if (kr <= 4) {
+            e = launch_cand_knn<4, false>(idx, ql, s);
+        } else {
+            e = launch_cand_knn<8, false>(idx, ql, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
         if (kr <= 1)
             e = launch_overflow<1>(idx, ql, s);
@@ -1395,6 +1596,30 @@ int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *
     else
         e = launch_vote_with_counter<8>(idx, ql, s, work);
     if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
+    return MRPT_OK;
+}
+
+}  // namespace mrpt
+
+namespace mrpt {
+
+int make_bf16_copy(mrpt_index *idx) {
+    const int64_t count = idx->n * int64_t(idx->dpad);
+    if (!idx->Xb) {
+        int rc = dev_alloc(reinterpret_cast<void **>(&idx->Xb), size_t(count) * 2, "bfloat16 copy");
+        if (rc) return rc;
+        idx->device_bytes += count * 2;
+    }
+    const int blocks = int(std::min<int64_t>((count + 255) / 256, 152 * 16));
+    uint32_t *flag = idx->status + 6;
+    MRPT_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(uint32_t), idx->stream));
+    k_to_bf16<<<blocks, 256, 0, idx->stream>>>(idx->X, reinterpret_cast<__nv_bfloat16 *>(idx->Xb), count,
+                                                flag);
+    MRPT_CUDA_TRY(cudaGetLastError());
+    uint32_t lossy = 1;
+    MRPT_CUDA_TRY(cudaMemcpyAsync(&lossy, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, idx->stream));
+    MRPT_CUDA_TRY(cudaStreamSynchronize(idx->stream));
+    idx->bf16_exact = lossy == 0;
     return MRPT_OK;
 }
 

@@ -1,0 +1,85 @@
+"""GPU: bfloat16 candidate distances with float32 re-rank (the reduced-
+precision form of the exact search on S).  The routing, votes and S are the
+float32 path's, so the checks are on the k-NN rows:
+
+* data exactly representable in bfloat16 (integers 0..255): the same rows as
+  the oracle (distances within 1e-5, ids up to ties);
+* general data: every returned distance is the exact float32 distance of its
+  id, rows are sorted, ids belong to S, and recall against the oracle's
+  float64 answer stays at least 0.99 with a 32-candidate margin.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import REL_TOL, check_results, oracle_sets
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_06957_gb300 as m
+    m.load_library()
+    return m
+
+
+def _query(mr, idx, Q, k, v, **kw):
+    ids, d = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, **kw)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), d.cpu().numpy()
+
+
+@pytest.mark.parametrize("margin", [0, 8])
+def test_bf16_exact_data_matches_oracle(mr, margin):
+    X, Q = workloads.mnist_like(5000, 60, seed=4)
+    T, l, v, k = 20, 5, 3, 10
+    dens = float(np.float32(784 ** -0.5))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, dens, 5)
+    mr.mrpt_add_lowp(idx)
+    gi, gd = _query(mr, idx, Q, k, v, precision=mr.MRPT_PREC_BF16, margin=margin)
+    ref = oracle.grow_trees(X, T, l, dens, 5)
+    oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, want_internals=True)
+    check_results(X, Q, gi, gd, oi, od, oracle_sets(ref, oleaf, v))
+    idx.close()
+
+
+def test_bf16_general_data_rerank(mr):
+    X, Q = workloads.gaussian_mixture(8000, 64, 80, n_centres=20, sigma=0.5, seed=6)
+    T, l, v, k = 16, 6, 2, 10
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, 0.0, 1)
+    mr.mrpt_add_lowp(idx)
+    gi, gd = _query(mr, idx, Q, k, v, precision=mr.MRPT_PREC_BF16, margin=32)
+    ref = oracle.grow_trees(X, T, l, float(np.float32(64 ** -0.5)), 1)
+    oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, want_internals=True)
+    sets = oracle_sets(ref, oleaf, v)
+    fin = np.isfinite(gd)
+    assert np.array_equal(fin, np.isfinite(od))
+    hits = 0
+    for i in range(len(Q)):
+        got = gi[i][fin[i]]
+        assert set(got.tolist()) <= sets[i]
+        ex = np.sqrt(((X[got].astype(np.float64) - Q[i].astype(np.float64)) ** 2).sum(1))
+        np.testing.assert_allclose(gd[i][fin[i]], ex, rtol=REL_TOL)
+        assert np.all(np.diff(gd[i][fin[i]]) >= 0)
+        hits += len(set(got.tolist()) & set(oi[i][fin[i]].tolist()))
+    assert hits / fin.sum() >= 0.99
+    idx.close()
+
+
+def test_bf16_needs_the_copy(mr):
+    X, Q = workloads.gaussian_mixture(500, 16, 4, seed=2)
+    idx = mr.mrpt_build(X, 4, 3, 0.3, 0)
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_query_ex(idx, Q, 5, 1, precision=mr.MRPT_PREC_BF16)
+    assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+    mr.mrpt_add_lowp(idx)
+    with pytest.raises(mr.MRPTError):
+        mr.mrpt_query_ex(idx, Q, 5, 1, precision=mr.MRPT_PREC_BF16, margin=300)
+    ids, _ = mr.mrpt_query_ex(idx, Q, 5, 1, precision=mr.MRPT_PREC_BF16, margin=4)
+    assert ids.shape == (4, 5)
+    idx.close()
