@@ -328,6 +328,15 @@ def run_gpu(args):
         rooflines.append(r_search)
     roofline = max(rooflines, key=lambda r: r["avg_ms"])
     others = [r for r in rooflines if r is not roofline]
+    # whole query path: B_q = T ceil(n/2^l) 4 (leaf ids) + |S| d b (candidate
+    # rows, b bytes per value) + d 4 (query) + k 8 (output) [+ re-rank rows],
+    # over the step's device time
+    path_bytes = leaf_bytes + row_bytes + d * 4 + k * 8
+    step_ms = total_ms / args.steps
+    path_roofline = {"bound": "hbm", "achieved": round(path_bytes * m / (step_ms / 1e3) / 1e9, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(path_bytes * m / (step_ms / 1e3) / 1e9 / peak, 4),
+                     "bytes_per_query": round(path_bytes, 1)}
 
     out = None
     if rank == 0:
@@ -353,6 +362,7 @@ def run_gpu(args):
             "gpu_launches": (2 if args.path == 1 else 4) * args.steps,
             "roofline": roofline,
             "roofline_other_kernels": others,
+            "path_roofline": path_roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "stage_ms": {"route": round(statistics.mean(route_ms), 4),
