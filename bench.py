@@ -51,11 +51,18 @@ def dist_env():
     return world, rank, local
 
 
-def shard_range(m: int, world: int, rank: int):
-    """Queries [lo, hi) of rank `rank` when m queries are split evenly."""
-    base, extra = divmod(m, world)
-    lo = rank * base + min(rank, extra)
-    return lo, lo + base + (1 if rank < extra else 0)
+def aggregate(local_ms: float, units_per_rank: int, steps: int, world: int, device=None):
+    """Replicas: every rank answers its own batch.  The job's time is the
+    slowest rank's (max over ranks, over the default process group when
+    world > 1); the job's throughput counts every rank's units."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * units_per_rank * steps / (total_ms / 1e3)
 
 
 def load_peaks():
@@ -279,13 +286,7 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.summary()
-    total_ms = sum(per_step)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * m * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate(sum(per_step), m, args.steps, world, dev)
     recall_strict, recall_ta = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
 
     # ---- end to end through the public API with host buffers

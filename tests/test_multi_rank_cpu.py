@@ -1,0 +1,54 @@
+"""The multi-GPU form is replicas (every rank answers its own query batch,
+no collective on the path).  Its host logic -- the max-over-ranks time and
+the job-wide throughput -- runs here on two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = 100.0 + 50.0 * rank          # rank 1 is the slow one
+    total_ms, value = bench.aggregate(local_ms, 10000, 4, world)
+    dist.barrier()
+    q.put((rank, total_ms, value))
+    dist.destroy_process_group()
+
+
+def test_replica_timing_is_max_over_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 2
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, total_ms, value in res:
+        assert total_ms == 150.0
+        assert abs(value - world * 10000 * 4 / 0.150) < 1e-6
+
+
+def test_single_rank_aggregate():
+    import bench
+    total_ms, value = bench.aggregate(200.0, 10000, 5, 1)
+    assert total_ms == 200.0 and abs(value - 250000.0) < 1e-9
