@@ -404,6 +404,75 @@ def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec=0, margin
             "h2d_bytes_per_step": int(m * d * 4), "d2h_bytes_per_step": int(m * k * 8)}
 
 
+def run_stream(args):
+    """Uneven query stream on the 60k x 784 index: 100,000 queries in batches
+    of floor(exp(U(0, ln 4097))) clamped to [1, 4096], k in {1, 10, 100} and
+    v in {2, 5, 8} drawn per batch.  Every batch is one plan run (a CUDA
+    graph); the same stream through plain mrpt_query_ex calls is timed too.
+    Reports queries/s and p50/p99 batch latency (device events)."""
+    import torch
+    import paper_1509_06957_gb300 as mr
+    W = WORKLOAD
+    dev = torch.device("cuda", 0)
+    X_np, Q_np = workloads.mnist_like(W["n"], W["m"], seed=W["seed"])
+    X = torch.from_numpy(X_np).to(dev)
+    Q = torch.from_numpy(Q_np).to(dev)
+    T_use = args.T or 100
+    index = mr.mrpt_build(X, T_use, W["l"], 0.0, seed=W["seed"])
+    mr.mrpt_add_lowp(index)
+    batches = workloads.uneven_batches(args.stream_queries, seed=1)
+    mmax = max(b for b, _, _ in batches)
+    out_ids = torch.empty((mmax, 100), dtype=torch.int32, device=dev)
+    out_d = torch.empty((mmax, 100), dtype=torch.float32, device=dev)
+    res = {}
+    for prec in (0, 1):
+        plans = {}
+        for kk in (1, 10, 100):
+            for vv in (2, 5, 8):
+                plans[(kk, vv)] = mr.Plan(index, mmax, kk, vv, precision=prec)
+        for mode in ("graph", "calls"):
+            def one(bi, b, kk, vv):
+                s0 = (bi * 977) % (Q.shape[0] - b + 1)
+                q = Q[s0:s0 + b]
+                oi = out_ids[:b, :kk]
+                od = out_d[:b, :kk]
+                if mode == "graph":
+                    plans[(kk, vv)].run(q, oi.contiguous(), od.contiguous())
+                else:
+                    mr.mrpt_query_ex(index, q, kk, vv, precision=prec)
+            for bi, (b, kk, vv) in enumerate(batches[:20]):
+                one(bi, b, kk, vv)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in batches]
+            t0 = time.perf_counter()
+            for bi, (b, kk, vv) in enumerate(batches):
+                evs[bi][0].record()
+                one(bi, b, kk, vv)
+                evs[bi][1].record()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            lat = np.array([a.elapsed_time(z) for a, z in evs])
+            res[f"{'bf16' if prec else 'fp32'}_{mode}"] = {
+                "queries_per_s": round(args.stream_queries / wall, 1),
+                "p50_batch_ms": round(float(np.percentile(lat, 50)), 4),
+                "p99_batch_ms": round(float(np.percentile(lat, 99)), 4),
+                "mean_batch_ms": round(float(lat.mean()), 4)}
+        for p_ in plans.values():
+            p_.close()
+    best = max(res.values(), key=lambda r: r["queries_per_s"])
+    out = {"metric": "queries/sec on an uneven batch stream (mnist-like 60000x784 index, batches 1..4096)",
+           "value": best["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic",
+           "config": {"workload": "uneven stream: 100k queries, batch sizes log-uniform 1..4096, "
+                                  "k in {1,10,100}, v in {2,5,8}", "T": T_use, "depth": W["l"],
+                      "batches": len(batches)},
+           "modes": res}
+    print(json.dumps(out), flush=True)
+    index.close()
+    return out
+
+
 # ------------------------------------------------------- CPU (oracle) -----
 
 def _oracle_index(X, T, l, seed):
@@ -499,6 +568,9 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["batch", "stream"], default="batch",
+                    help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
+    ap.add_argument("--stream-queries", type=int, default=100000)
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto",
                     help="candidate-distance precision (auto: the faster at the recall target)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1],
@@ -512,6 +584,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "stream":
+        run_stream(args)
     else:
         run_gpu(args)
 

@@ -150,6 +150,32 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
  */
 int mrpt_add_lowp(mrpt_index *idx, int32_t precision);
 
+/*
+ * Query plans: the whole query (counter clears and every kernel) captured
+ * once into a CUDA graph and replayed per batch, which removes the per-call
+ * launch work for streams of small, uneven batches.  A plan fixes k, v and
+ * the options (n_trees, path, precision, margin, chunk, ring; debug outputs
+ * and stage_ms are not available) and a largest batch m_max; it owns its
+ * scratch, so plans of one index may run on different streams.  The kernels
+ * read each batch's query pointer, output pointers and size from a small
+ * device record, so one graph serves every m <= m_max.
+ *
+ * mrpt_plan_create -- capture the plan (synchronous; allocates).
+ * mrpt_plan_run    -- answer m <= m_max queries, exactly as mrpt_query_ex
+ *                     with the plan's options.  Buffers may be host or device
+ *                     memory (host buffers are staged; the call then returns
+ *                     after the results are in place).  Runs on the index's
+ *                     stream at the time of the call.
+ * mrpt_plan_free   -- release the plan (NULL is accepted).
+ * Errors: INVALID_ARG, OOM, CUDA (and as mrpt_query).
+ */
+typedef struct mrpt_plan mrpt_plan;
+int mrpt_plan_create(mrpt_index *idx, int64_t m_max, int32_t k, int32_t v,
+                     const mrpt_query_opts *opts, mrpt_plan **out);
+int mrpt_plan_run(mrpt_plan *plan, const float *Q, int64_t m, int32_t *out_ids,
+                  float *out_dists);
+int mrpt_plan_free(mrpt_plan *plan);
+
 /* Release the index and everything it owns.  NULL is accepted. */
 int mrpt_free(mrpt_index *idx);
 

@@ -51,6 +51,7 @@ ABI_SYMBOLS = (
     "mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
     "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
+    "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free",
 )
 MRPT_PREC_FP32 = 0
 MRPT_PREC_BF16 = 1
@@ -139,6 +140,13 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_export.argtypes = [vp, i32, vp, i64]
         lib.mrpt_debug_fail_alloc_after.restype = ctypes.c_int
         lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
+        lib.mrpt_plan_create.restype = ctypes.c_int
+        lib.mrpt_plan_create.argtypes = [vp, i64, i32, i32, ctypes.POINTER(QueryOpts),
+                                         ctypes.POINTER(vp)]
+        lib.mrpt_plan_run.restype = ctypes.c_int
+        lib.mrpt_plan_run.argtypes = [vp, vp, i64, vp, vp]
+        lib.mrpt_plan_free.restype = ctypes.c_int
+        lib.mrpt_plan_free.argtypes = [vp]
         lib.mrpt_add_lowp.restype = ctypes.c_int
         lib.mrpt_add_lowp.argtypes = [vp, i32]
         lib.mrpt_query_noalloc.restype = ctypes.c_int
@@ -385,3 +393,56 @@ def mrpt_query_noalloc(index: Index, Q, k: int, v: int, out_ids, out_dists,
         _check(lib.mrpt_set_stream(index.handle, stream))
     _check(lib.mrpt_query_noalloc(index.handle, _ptr(Q), Q.shape[0], k, v, int(n_trees),
                                   _ptr(out_ids), _ptr(out_dists)))
+
+
+class Plan:
+    """A query captured into a CUDA graph (mrpt_plan_create): fixed k, v and
+    options, any batch of up to m_max queries per run."""
+
+    def __init__(self, index: Index, m_max: int, k: int, v: int, n_trees: int = 0, path: int = 0,
+                 precision: int = 0, margin: int = 0, chunk: int = 0, ring: int = 0):
+        self._lib = load_library()
+        self.index, self.m_max, self.k, self.v = index, m_max, k, v
+        opts = QueryOpts()
+        opts.n_trees, opts.path, opts.precision = int(n_trees), int(path), int(precision)
+        opts.margin, opts.chunk, opts.ring = int(margin), int(chunk), int(ring)
+        h = ctypes.c_void_p()
+        _check(self._lib.mrpt_plan_create(index.handle, int(m_max), int(k), int(v),
+                                          ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, Q, out_ids=None, out_dists=None):
+        Q = _as_f32(Q)
+        m = Q.shape[0]
+        if out_ids is None:
+            out_ids = _empty_like_input(Q, (m, self.k), np.int32)
+        if out_dists is None:
+            out_dists = _empty_like_input(Q, (m, self.k), np.float32)
+        stream = _current_stream(Q)
+        if stream is not None:
+            _check(self._lib.mrpt_set_stream(self.index.handle, stream))
+        _check(self._lib.mrpt_plan_run(self._h, _ptr(Q), m, _ptr(out_ids), _ptr(out_dists)))
+        return out_ids, out_dists
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(self._lib.mrpt_plan_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mrpt_plan_create(index: Index, m_max: int, k: int, v: int, **opts) -> Plan:
+    return Plan(index, m_max, k, v, **opts)
+
+
+def mrpt_plan_run(plan: Plan, Q, out_ids=None, out_dists=None):
+    return plan.run(Q, out_ids, out_dists)
+
+
+def mrpt_plan_free(plan: Plan) -> None:
+    plan.close()

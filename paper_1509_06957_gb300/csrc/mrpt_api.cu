@@ -102,7 +102,72 @@ static void free_index(mrpt_index *idx) {
     delete idx;
 }
 
+// Scratch of the two-kernel query path for m queries: candidate lists,
+// work items, per-chunk partial top-k lists, |S|, overflow list and
+// per-query completion counters, each starting on a 256-byte boundary.
+struct CandLayout {
+    int32_t capq, chunk, max_items_q, ring;
+    size_t lb, ib, pb, nb, total;
+};
+
+static CandLayout cand_layout(const mrpt_index *idx, int64_t m, int32_t k, int32_t v,
+                              int32_t n_trees, int32_t precision, int32_t margin,
+                              const mrpt_query_opts *opts) {
+    CandLayout L{};
+    const int64_t ks = int64_t(k) + margin;  // list length kept per chunk
+    // |S| <= T ceil(n / 2^l) / v (Sec. III-B: every member of S holds at
+    // least v of the T ceil(n / 2^l) votes), and |S| <= n
+    const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
+    int64_t bound = int64_t(n_trees) * leaf_max / v;
+    if (bound > idx->n) bound = idx->n;
+    L.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
+    if (L.capq < 1) L.capq = 1;
+    // candidate-search work items: chunks of a list, at least 2(k + margin)
+    // candidates and 64 (float32) or 32 (bfloat16) each
+    L.chunk = int32_t(std::max<int64_t>(precision == MRPT_PREC_BF16 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
+    if (opts && opts->chunk > 0) L.chunk = int32_t(std::max<int64_t>(opts->chunk, ks));
+    L.ring = (opts && opts->ring > 0) ? std::min<int32_t>(std::max<int32_t>(opts->ring, 2), 16) : 0;
+    L.max_items_q = (L.capq + L.chunk - 1) / L.chunk;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    L.lb = up(size_t(m) * size_t(L.capq) * 4);
+    L.ib = up(size_t(m) * size_t(L.max_items_q) * 8);
+    L.pb = up(size_t(m) * size_t(L.max_items_q) * size_t(ks) * 4);
+    L.nb = up(size_t(m) * 4);
+    L.total = L.lb + L.ib + 2 * L.pb + 3 * L.nb;
+    return L;
+}
+
+static void cand_carve(const CandLayout &L, char *base, int64_t m, QueryLaunch &ql) {
+    (void)m;
+    ql.capq = L.capq;
+    ql.chunk = L.chunk;
+    ql.max_items_q = L.max_items_q;
+    ql.ring = L.ring;
+    ql.cand_list = reinterpret_cast<int32_t *>(base);
+    ql.items = reinterpret_cast<int2 *>(base + L.lb);
+    ql.part_d = reinterpret_cast<float *>(base + L.lb + L.ib);
+    ql.part_i = reinterpret_cast<int32_t *>(base + L.lb + L.ib + L.pb);
+    ql.ncand = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb);
+    ql.overflow = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb + L.nb);
+    ql.done = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb + 2 * L.nb);
+}
+
 }  // namespace mrpt
+
+// A captured query graph and everything it reads or writes.
+struct mrpt_plan {
+    mrpt_index *idx = nullptr;
+    int64_t m_max = 0;
+    int32_t k = 0, v = 0, n_trees = 0;
+    mrpt::Scratch buf;          // record, counters, staging, query scratch
+    mrpt::QueryRecord *rec = nullptr;
+    uint32_t *counters = nullptr;
+    float *q_stage = nullptr;
+    int32_t *ids_stage = nullptr;
+    float *dists_stage = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 using namespace mrpt;
 
@@ -390,35 +455,9 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
     ql.precision = precision;
     ql.margin = margin;
     if (ql.path == 0) {
-        const int64_t ks = int64_t(k) + margin;  // list length kept per chunk
-        // |S| <= T ceil(n / 2^l) / v (Sec. III-B: every member of S holds at
-        // least v of the T ceil(n / 2^l) votes), and |S| <= n
-        const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
-        int64_t bound = int64_t(n_trees) * leaf_max / v;
-        if (bound > idx->n) bound = idx->n;
-        ql.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
-        if (ql.capq < 1) ql.capq = 1;
-        // candidate-search work items: chunks of a list, at least 128 and at
-        // least 2(k + margin) candidates each
-        ql.chunk = int32_t(std::max<int64_t>(precision == MRPT_PREC_BF16 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
-        if (opts && opts->chunk > 0) ql.chunk = int32_t(std::max<int64_t>(opts->chunk, ks));
-        ql.ring = (opts && opts->ring > 0) ? std::min<int32_t>(std::max<int32_t>(opts->ring, 2), 16) : 0;
-        ql.max_items_q = (ql.capq + ql.chunk - 1) / ql.chunk;
-        // sub-buffers, each starting on a 256-byte boundary
-        auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-        const size_t lb = up(size_t(m) * size_t(ql.capq) * 4);                  // lists
-        const size_t ib = up(size_t(m) * size_t(ql.max_items_q) * 8);           // items
-        const size_t pb = up(size_t(m) * size_t(ql.max_items_q) * size_t(ks) * 4);  // each partial array
-        const size_t nb = up(size_t(m) * 4);                                    // ncand, overflow, done
-        if ((rc = idx->q_cand.ensure(lb + ib + 2 * pb + 3 * nb, "candidate lists"))) return rc;
-        char *base = static_cast<char *>(idx->q_cand.ptr);
-        ql.cand_list = reinterpret_cast<int32_t *>(base);
-        ql.items = reinterpret_cast<int2 *>(base + lb);
-        ql.part_d = reinterpret_cast<float *>(base + lb + ib);
-        ql.part_i = reinterpret_cast<int32_t *>(base + lb + ib + pb);
-        ql.ncand = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb);
-        ql.overflow = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb + nb);
-        ql.done = reinterpret_cast<int32_t *>(base + lb + ib + 2 * pb + 2 * nb);
+        const CandLayout lay = cand_layout(idx, m, k, v, n_trees, precision, margin, opts);
+        if ((rc = idx->q_cand.ensure(lay.total, "candidate lists"))) return rc;
+        cand_carve(lay, static_cast<char *>(idx->q_cand.ptr), m, ql);
     }
 
     if ((rc = launch_query(idx, ql))) return rc;
@@ -446,6 +485,157 @@ int mrpt_add_lowp(mrpt_index *idx, int32_t precision) {
 int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v, int32_t *out_ids,
                float *out_dists) {
     return mrpt_query_ex(idx, Q, m, k, v, nullptr, out_ids, out_dists);
+}
+
+int mrpt_plan_free(mrpt_plan *plan) {
+    clear_error();
+    if (!plan) return MRPT_OK;
+    if (plan->idx) cudaStreamSynchronize(plan->idx->stream);
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    plan->buf.release();
+    delete plan;
+    return MRPT_OK;
+}
+
+int mrpt_plan_create(mrpt_index *idx, int64_t m_max, int32_t k, int32_t v,
+                     const mrpt_query_opts *opts, mrpt_plan **out) {
+    clear_error();
+    if (!out || !idx) {
+        set_error("mrpt_plan_create: NULL argument");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const int32_t n_trees = (opts && opts->n_trees > 0) ? opts->n_trees : idx->T;
+    const int32_t path = opts ? opts->path : 0;
+    const int32_t precision = opts ? opts->precision : MRPT_PREC_FP32;
+    const int32_t margin = (opts && precision == MRPT_PREC_BF16) ? opts->margin : 0;
+    if (m_max < 1 || k < 1 || k > MRPT_MAX_K || v < 1 || n_trees > idx->T || v > n_trees ||
+        (path != 0 && path != 1) || (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16) ||
+        (precision == MRPT_PREC_BF16 && (!idx->Xb || path != 0 || margin < 0 || k + margin > MRPT_MAX_K)) ||
+        (opts && (opts->chunk < 0 || opts->ring < 0 || opts->proj || opts->leaf || opts->votes ||
+                  opts->n_cand || opts->cand || opts->stage_ms))) {
+        set_error("mrpt_plan_create: invalid argument (need m_max >= 1, 1 <= k <= " +
+                  std::to_string(MRPT_MAX_K) +
+                  ", 1 <= v <= n_trees <= T, a valid path/precision, no debug outputs)");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    mrpt_plan *plan = new (std::nothrow) mrpt_plan();
+    if (!plan) {
+        set_error("mrpt_plan_create: host allocation failed");
+        return MRPT_ERR_OOM;
+    }
+    plan->idx = idx;
+    plan->m_max = m_max;
+    plan->k = k;
+    plan->v = v;
+    plan->n_trees = n_trees;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t rec_b = 256, ctr_b = 256;
+    const size_t q_b = up(size_t(m_max) * size_t(idx->d) * 4);
+    const size_t o_b = up(size_t(m_max) * size_t(k) * 4);
+    const size_t leaf_b = up(size_t(m_max) * size_t(n_trees) * 4);
+    CandLayout lay{};
+    if (path == 0) lay = cand_layout(idx, m_max, k, v, n_trees, precision, margin, opts);
+    int rc = plan->buf.ensure(rec_b + ctr_b + q_b + 2 * o_b + leaf_b + lay.total, "query plan");
+    if (rc) {
+        delete plan;
+        return rc;
+    }
+    char *base = static_cast<char *>(plan->buf.ptr);
+    plan->rec = reinterpret_cast<QueryRecord *>(base);
+    plan->counters = reinterpret_cast<uint32_t *>(base + rec_b);
+    plan->q_stage = reinterpret_cast<float *>(base + rec_b + ctr_b);
+    plan->ids_stage = reinterpret_cast<int32_t *>(base + rec_b + ctr_b + q_b);
+    plan->dists_stage = reinterpret_cast<float *>(base + rec_b + ctr_b + q_b + o_b);
+    int32_t *leaf = reinterpret_cast<int32_t *>(base + rec_b + ctr_b + q_b + 2 * o_b);
+    char *cand_base = base + rec_b + ctr_b + q_b + 2 * o_b + leaf_b;
+
+    QueryLaunch ql{};
+    ql.Q = plan->q_stage;
+    ql.m = m_max;
+    ql.k = k;
+    ql.v = v;
+    ql.n_trees = n_trees;
+    ql.out_ids = plan->ids_stage;
+    ql.out_dists = plan->dists_stage;
+    ql.leaf = leaf;
+    ql.path = path;
+    ql.precision = precision;
+    ql.margin = margin;
+    if (path == 0) cand_carve(lay, cand_base, m_max, ql);
+    ql.counters = plan->counters;
+    ql.rec = plan->rec;
+    ql.use_stream = true;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->counters, 0, ctr_b, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        mrpt_plan_free(plan);
+        return cuda_fail(e, "mrpt_plan_create: stream");
+    }
+    ql.stream = cs;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = launch_query(idx, ql);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        plan->graph = g;
+        if (rc == MRPT_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "mrpt_plan_create: capture");
+    } else {
+        rc = cuda_fail(e, "mrpt_plan_create: begin capture");
+    }
+    if (rc == MRPT_OK) {
+        e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "mrpt_plan_create: instantiate");
+    }
+    cudaStreamDestroy(cs);
+    if (rc != MRPT_OK) {
+        mrpt_plan_free(plan);
+        return rc;
+    }
+    *out = plan;
+    return MRPT_OK;
+}
+
+int mrpt_plan_run(mrpt_plan *plan, const float *Q, int64_t m, int32_t *out_ids, float *out_dists) {
+    clear_error();
+    if (!plan) {
+        set_error("mrpt_plan_run: plan is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (m < 0 || m > plan->m_max || (m > 0 && (!Q || !out_ids || !out_dists))) {
+        set_error("mrpt_plan_run: need 0 <= m <= m_max and non-NULL buffers");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (m == 0) return MRPT_OK;
+    mrpt_index *idx = plan->idx;
+    cudaStream_t s = idx->stream;
+    const size_t qb = size_t(m) * size_t(idx->d) * 4;
+    const size_t ob = size_t(m) * size_t(plan->k) * 4;
+    bool any_host = false;
+    QueryRecord r{};
+    r.m = m;
+    if (is_device_ptr(Q)) {
+        r.Q = Q;
+    } else {
+        any_host = true;
+        MRPT_CUDA_TRY(cudaMemcpyAsync(plan->q_stage, Q, qb, cudaMemcpyHostToDevice, s));
+        r.Q = plan->q_stage;
+    }
+    const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);
+    any_host = any_host || !ids_dev || !dists_dev;
+    r.out_ids = ids_dev ? out_ids : plan->ids_stage;
+    r.out_dists = dists_dev ? out_dists : plan->dists_stage;
+    int rc = set_record(plan->rec, r, s);
+    if (rc) return rc;
+    MRPT_CUDA_TRY(cudaGraphLaunch(plan->exec, s));
+    if (!ids_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_ids, plan->ids_stage, ob, cudaMemcpyDeviceToHost, s));
+    if (!dists_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_dists, plan->dists_stage, ob, cudaMemcpyDeviceToHost, s));
+    if (any_host) return mrpt_sync(idx);
+    return MRPT_OK;
 }
 
 int64_t mrpt_export_size(const mrpt_index *idx, int32_t what) {

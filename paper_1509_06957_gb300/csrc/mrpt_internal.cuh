@@ -105,6 +105,16 @@ int check_finite(const float *X, int64_t rows, int32_t stride, int32_t cols, cud
 
 // ------------------------------------------------------ query (mrpt_query.cu)
 
+// One batch as a captured query graph sees it: the kernels read the query
+// pointer, output pointers and batch size from this device-resident record
+// (plan mode) instead of their launch arguments.
+struct QueryRecord {
+    const float *Q;
+    int32_t *out_ids;
+    float *out_dists;
+    int64_t m;
+};
+
 struct QueryLaunch {
     const float *Q;        // m x d device queries
     int64_t m;
@@ -132,6 +142,10 @@ struct QueryLaunch {
     int32_t precision;     // 0 float32 rows, 1 bfloat16 rows + float32 re-rank
     int32_t margin;        // survivors beyond k kept for the re-rank
     int32_t ring;          // candidate rows staged per search warp (0 = auto)
+    uint32_t *counters;    // 8 work-counter words ([0] unused); null = the index's
+    cudaStream_t stream;   // stream of the launches (plans capture on their own)
+    bool use_stream;       // take `stream` instead of the index's stream
+    const QueryRecord *rec;  // plan mode: batch read on the device (m <= ql.m)
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);
@@ -142,5 +156,8 @@ int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *
 
 // Fills idx->Xb with X rounded to bfloat16 (allocating it on first use).
 int make_bf16_copy(mrpt_index *idx);
+
+// Stream-ordered write of a plan's batch record.
+int set_record(QueryRecord *rec, const QueryRecord &r, cudaStream_t s);
 
 }  // namespace mrpt

@@ -42,9 +42,15 @@ __global__ void __launch_bounds__(512) k_query_route(
     const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
     const int32_t *__restrict__ col_off, const int32_t *__restrict__ dim,
     const float *__restrict__ val, const float *__restrict__ split, int32_t *__restrict__ leaf,
-    float *__restrict__ proj, uint32_t *__restrict__ status, int64_t n_items) {
+    float *__restrict__ proj, uint32_t *__restrict__ status, int64_t n_items,
+    const QueryRecord *__restrict__ rec) {
     extern __shared__ float qs[];  // QB x (d | 1)
     const int stride = d | 1;
+    if (rec != nullptr) {
+        Q = rec->Q;
+        m = rec->m;
+        n_items = ((m + QB - 1) / QB) * ((T_use + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM);
+    }
     constexpr int G = 32 / QB;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -433,6 +439,7 @@ struct VoteSearchArgs {
     int32_t region_bytes;  // bytes of the counter / merge region (multiple of 16)
     const int32_t *qlist;        // optional: process only these queries ...
     const uint32_t *qlist_len;   // ... this many of them (read on the device)
+    const QueryRecord *rec;      // plan mode: Q, outputs and m of the batch
 };
 
 // Per warp: a buffer of emitted candidates waiting for their distances.
@@ -452,7 +459,14 @@ constexpr int WBUF = 256;
 // computed as soon as it is emitted.  Ids above the chunk are left for the
 // next chunk through per-tree cursors (leaves list ids in ascending order).
 template <int KR>
-__global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchArgs a) {
+__global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchArgs a0) {
+    VoteSearchArgs a = a0;
+    if (a.rec != nullptr) {
+        a.Q = a.rec->Q;
+        a.out_ids = a.rec->out_ids;
+        a.out_dists = a.rec->out_dists;
+        a.m = a.rec->m;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);                        // a.cnt_words
     float *qv = reinterpret_cast<float *>(smem + size_t(a.region_bytes));      // dpad
@@ -739,9 +753,12 @@ struct VoteEmitArgs {
     uint32_t *n_items;
     int32_t chunk;         // candidates per work item
     int32_t *done;         // per query: finished work items
+    const QueryRecord *rec;  // plan mode: m of the batch
 };
 
-__global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs a) {
+__global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs a0) {
+    VoteEmitArgs a = a0;
+    if (a.rec != nullptr) a.m = a.rec->m;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words
     int32_t *cur = reinterpret_cast<int32_t *>(cnt + a.cnt_words);
@@ -935,10 +952,18 @@ struct CandKnnArgs {
     int32_t *done;
     float *part_d;         // partial top-k lists: m x max_items_q x k
     int32_t *part_i;
+    const QueryRecord *rec;  // plan mode: Q, outputs and m of the batch
 };
 
 template <int KR>
-__global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs a) {
+__global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs a0) {
+    CandKnnArgs a = a0;
+    if (a.rec != nullptr) {
+        a.Q = a.rec->Q;
+        a.out_ids = a.rec->out_ids;
+        a.out_dists = a.rec->out_dists;
+        a.m = a.rec->m;
+    }
     extern __shared__ __align__(16) float qsm[];  // CK_WARPS x dpad
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1001,7 +1026,14 @@ constexpr int CR_WARPS = 4;
 constexpr int CR_MAX_RING = 16;
 
 template <int KR, bool BF16>
-__global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a) {
+__global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0) {
+    CandKnnArgs a = a0;
+    if (a.rec != nullptr) {
+        a.Q = a.rec->Q;
+        a.out_ids = a.rec->out_ids;
+        a.out_dists = a.rec->out_dists;
+        a.m = a.rec->m;
+    }
     extern __shared__ __align__(16) unsigned char csm[];
     __shared__ __align__(8) uint64_t s_bar[CR_WARPS][CR_MAX_RING];
     const int lane = threadIdx.x & 31;
@@ -1271,7 +1303,7 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
     k_query_route<QB><<<unsigned(blocks), 512, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l,
                                                          idx->L, idx->col_off, idx->dim, idx->val,
                                                          idx->split, ql.leaf, ql.proj, idx->status,
-                                                         items);
+                                                         items, ql.rec);
     return cudaGetLastError();
 }
 
@@ -1318,6 +1350,7 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     a.work = work;
     a.cnt_words = cnt_words;
     a.region_bytes = int(region);
+    a.rec = ql.rec;
     return cudaSuccess;
 }
 
@@ -1326,9 +1359,10 @@ cudaError_t launch_vote(const mrpt_index *idx, const QueryLaunch &ql, cudaStream
     VoteSearchArgs a;
     size_t smem = 0;
     int64_t blocks = 0;
-    cudaError_t e = plan_vote<KR>(idx, ql, idx->status + 1, a, smem, blocks);
+    uint32_t *ctr = ql.counters ? ql.counters : idx->status;
+    cudaError_t e = plan_vote<KR>(idx, ql, ctr + 1, a, smem, blocks);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(idx->status + 1, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(ctr + 1, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
     return cudaGetLastError();
@@ -1389,11 +1423,13 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.capq = ql.capq;
     a.ncand = ql.ncand;
     a.overflow = ql.overflow;
-    a.n_overflow = idx->status + 3;
-    a.work = idx->status + 1;
+    uint32_t *ctr = ql.counters ? ql.counters : idx->status;
+    a.n_overflow = ctr + 3;
+    a.work = ctr + 1;
+    a.rec = ql.rec;
     a.cnt_words = cnt_words;
     a.items = ql.items;
-    a.n_items = idx->status + 5;
+    a.n_items = ctr + 5;
     a.chunk = ql.chunk;
     a.done = ql.done;
     a.dbg_votes = ql.votes;
@@ -1429,11 +1465,13 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.k = ql.k + (a.rerank ? ql.margin : 0);
     a.out_ids = ql.out_ids;
     a.out_dists = ql.out_dists;
-    a.work = idx->status + 2;
+    uint32_t *ctr = ql.counters ? ql.counters : idx->status;
+    a.work = ctr + 2;
     a.ring = ring;
     a.status = idx->status;
+    a.rec = ql.rec;
     a.items = ql.items;
-    a.n_items = idx->status + 5;
+    a.n_items = ctr + 5;
     a.chunk = ql.chunk;
     a.max_items_q = ql.max_items_q;
     a.done = ql.done;
@@ -1477,10 +1515,12 @@ cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     q2.votes = nullptr;
     q2.n_cand = nullptr;
     q2.cand = nullptr;
-    cudaError_t e = plan_vote<KR>(idx, q2, idx->status + 4, a, smem, blocks);
+    uint32_t *ctr = ql.counters ? ql.counters : idx->status;
+    cudaError_t e = plan_vote<KR>(idx, q2, ctr + 4, a, smem, blocks);
     if (e != cudaSuccess) return e;
     a.qlist = ql.overflow;
-    a.qlist_len = idx->status + 3;
+    a.qlist_len = ctr + 3;
+    a.rec = ql.rec;
     k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1488,7 +1528,7 @@ cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
 }  // namespace
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
-    cudaStream_t s = idx->stream;
+    cudaStream_t s = ql.use_stream ? ql.stream : idx->stream;
     if (ql.m == 0) return MRPT_OK;
     cudaError_t e;
     if (ql.stage_ms) {
@@ -1515,7 +1555,8 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     } else {
         // work counters [1] vote/emit, [2] candidate search, [3] overflow
         // length, [4] overflow pass, [5] candidate-search work items
-        MRPT_CUDA_TRY(cudaMemsetAsync(idx->status + 1, 0, 5 * sizeof(uint32_t), s));
+        MRPT_CUDA_TRY(cudaMemsetAsync((ql.counters ? ql.counters : idx->status) + 1, 0,
+                                      5 * sizeof(uint32_t), s));
         e = launch_vote_emit(idx, ql, s);
         if (e != cudaSuccess) return cuda_fail(e, "k_vote_emit");
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
@@ -1620,6 +1661,20 @@ int make_bf16_copy(mrpt_index *idx) {
     MRPT_CUDA_TRY(cudaMemcpyAsync(&lossy, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, idx->stream));
     MRPT_CUDA_TRY(cudaStreamSynchronize(idx->stream));
     idx->bf16_exact = lossy == 0;
+    return MRPT_OK;
+}
+
+}  // namespace mrpt
+
+namespace mrpt {
+
+// Writes a plan's batch record on the stream; the record travels in the
+// launch arguments, so the host object may be reused at once.
+__global__ void k_set_record(QueryRecord *rec, QueryRecord r) { *rec = r; }
+
+int set_record(QueryRecord *rec, const QueryRecord &r, cudaStream_t s) {
+    k_set_record<<<1, 1, 0, s>>>(rec, r);
+    MRPT_CUDA_TRY(cudaGetLastError());
     return MRPT_OK;
 }
 
