@@ -231,7 +231,8 @@ def run_gpu(args):
     dists = torch.empty((m, k), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    mr.mrpt_add_lowp(index)
+    mr.mrpt_add_lowp(index, mr.MRPT_PREC_BF16)
+    mr.mrpt_add_lowp(index, mr.MRPT_PREC_FP8)
 
     def query(T_use, v, stage=None, prec=0, margin=0):
         mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, out_ids=ids, out_dists=dists,
@@ -243,21 +244,24 @@ def run_gpu(args):
     stage = np.zeros(4, np.float32)
     grid = [(args.T, args.v)] if args.T and args.v else \
         [(T_, v_) for T_ in W["T_grid"] for v_ in W["v_grid"] if v_ <= T_]
-    precs = [(0, 0)] if args.path == 1 or args.precision == "fp32" else \
-        ([(1, m_) for m_ in (0, 8, 32)] if args.precision == "bf16" else
-         [(0, 0)] + [(1, m_) for m_ in (0, 8, 32)])
+    bf16 = [(1, m_) for m_ in (0, 8, 32)]
+    fp8 = [(2, m_) for m_ in (8, 32)]
+    precs = {"fp32": [(0, 0)], "bf16": bf16, "fp8": fp8,
+             "auto": [(0, 0)] + bf16 + fp8}[args.precision]
+    if args.path == 1:
+        precs = [(0, 0)]
     for T_use, v in grid:
         for prec, margin in precs:
             query(T_use, v, prec=prec, margin=margin)  # warm
             flush.zero_()
             query(T_use, v, stage, prec=prec, margin=margin)
             rs, rt = recall_at_k(ids, X, Q, gt_ids, gt_kth, torch)
-            sweep.append(dict(T=T_use, v=v, precision="bf16" if prec else "fp32", margin=margin,
+            sweep.append(dict(T=T_use, v=v, precision=("fp32", "bf16", "fp8")[prec], margin=margin,
                               ms=float(stage[3]), recall=round(rt, 4), recall_strict=round(rs, 4)))
     ok = [s for s in sweep if s["recall"] >= W["target_recall"]]
     best = min(ok, key=lambda s: s["ms"]) if ok else max(sweep, key=lambda s: s["recall"])
     T_use, v = best["T"], best["v"]
-    prec, margin = (1 if best["precision"] == "bf16" else 0), best["margin"]
+    prec, margin = ("fp32", "bf16", "fp8").index(best["precision"]), best["margin"]
     ok32 = [s for s in ok if s["precision"] == "fp32"]
     best32 = min(ok32, key=lambda s: s["ms"]) if ok32 else None
 
@@ -299,7 +303,11 @@ def run_gpu(args):
     peak, peak_kind = load_peaks()
     L = 1 << l
     leaf_bytes = T_use * math.ceil(n / L) * 4
-    row_bytes = mean_S * d * (2 if prec else 4) + (min(k + margin, mean_S) * d * 4 if prec else 0)
+    # candidate rows in the precision used, plus the float32 rows of the
+    # re-rank (skipped for a lossless bfloat16 copy of this integer data)
+    vbytes = (4, 2, 1)[prec]
+    rerank_rows = 0 if prec == 0 or (prec == 1) else min(k + margin, mean_S)
+    row_bytes = mean_S * (d * vbytes + (16 if prec == 2 else 0)) + rerank_rows * d * 4
     vote_avg = statistics.mean(vote_ms)
     search_avg = statistics.mean(search_ms)
     if args.path == 1:
@@ -347,11 +355,12 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16 rows, f32 accumulate + f32 re-rank" if prec else "f32",
+            "dtype": ("f32", "bf16 rows, f32 accumulate (lossless copy: no re-rank)",
+                      "e4m3 rows + per-row scale, f32 accumulate + f32 re-rank")[prec],
             "data": "synthetic",
             "config": {"workload": W["name"], "n": n, "d": d, "queries_per_step": m, "k": k,
                        "depth": l, "T": T_use, "v": v, "density": "1/sqrt(d)",
-                       "precision": "bf16" if prec else "fp32", "rerank_margin": margin,
+                       "precision": ("fp32", "bf16", "fp8")[prec], "rerank_margin": margin,
                        "fp32_best": best32,
                        "recall_at_10": round(recall_ta, 4),
                        "recall_at_10_strict": round(recall_strict, 4),
@@ -571,7 +580,7 @@ def main():
     ap.add_argument("--workload", choices=["batch", "stream"], default="batch",
                     help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
     ap.add_argument("--stream-queries", type=int, default=100000)
-    ap.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto",
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp8"], default="auto",
                     help="candidate-distance precision (auto: the faster at the recall target)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1],
                     help="0: vote/emit + candidate search kernels, 1: one fused kernel")

@@ -107,13 +107,14 @@ typedef struct mrpt_query_opts {
     int32_t n_trees;      /* use the first n_trees trees (0 = all T) */
     int32_t path;         /* 0: vote/emit kernel + candidate-search kernel (default);
                              1: one fused vote + search kernel.  Same results. */
-    int32_t precision;    /* MRPT_PREC_FP32 (0, default) or MRPT_PREC_BF16 (1): candidate
-                             distances from the index's bfloat16 copy (mrpt_add_lowp),
-                             accumulated in float32; the k + margin nearest by that
-                             distance are then re-ranked with exact float32 distances.
-                             When the copy is lossless (every value exactly a bfloat16)
-                             those distances are the float32 ones up to summation order
-                             and the re-rank is skipped.  Path 0 only; a query whose
+    int32_t precision;    /* MRPT_PREC_FP32 (0, default), MRPT_PREC_BF16 (1) or
+                             MRPT_PREC_FP8 (2): candidate distances from the index's
+                             reduced-precision copy (mrpt_add_lowp), accumulated in
+                             float32; the k + margin nearest by that distance are then
+                             re-ranked with exact float32 distances.  When the bfloat16
+                             copy is lossless (every value exactly a bfloat16) those
+                             distances are the float32 ones up to summation order and
+                             the re-rank is skipped.  Path 0 only; a query whose
                              candidate list overflows is answered in float32
                              throughout. */
     int32_t margin;       /* survivors beyond k kept for the re-rank (k + margin <= 256) */
@@ -140,13 +141,16 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
 
 #define MRPT_PREC_FP32 0
 #define MRPT_PREC_BF16 1
+#define MRPT_PREC_FP8 2
 
 /*
  * mrpt_add_lowp -- add a reduced-precision copy of the data to the index for
  * the candidate distances of later queries (mrpt_query_opts.precision).
  * MRPT_PREC_BF16: every value rounded to bfloat16 (nearest even), same row
- * layout, 2 bytes per value on the device.  The float32 data stays in the
- * index for the re-rank.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ * layout, 2 bytes per value.  MRPT_PREC_FP8: each row scaled by
+ * 448 / max|x| and rounded to e4m3 (saturating), 1 byte per value plus the
+ * row's float32 scale (rows padded to 16 bytes).  The float32 data stays in
+ * the index for the re-rank.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA.
  */
 int mrpt_add_lowp(mrpt_index *idx, int32_t precision);
 

@@ -55,6 +55,7 @@ ABI_SYMBOLS = (
 )
 MRPT_PREC_FP32 = 0
 MRPT_PREC_BF16 = 1
+MRPT_PREC_FP8 = 2
 MRPT_NOALLOC_MAX_LEAF_ENTRIES = 1048512
 
 
@@ -265,7 +266,8 @@ def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0) -> Ind
 
 
 def mrpt_add_lowp(index: Index, precision: int = MRPT_PREC_BF16) -> None:
-    """Add a bfloat16 copy of the data for reduced-precision distances."""
+    """Add a bfloat16 (MRPT_PREC_BF16) or e4m3 + per-row scale
+    (MRPT_PREC_FP8) copy of the data for reduced-precision distances."""
     _check(load_library().mrpt_add_lowp(index.handle, int(precision)))
 
 

@@ -91,6 +91,7 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->leaf_off);
     cudaFree(idx->leaf_ids);
     cudaFree(idx->Xb);
+    cudaFree(idx->X8);
     cudaFree(idx->status);
     for (cudaEvent_t &ev : idx->ev)
         if (ev) cudaEventDestroy(ev);
@@ -124,7 +125,7 @@ static CandLayout cand_layout(const mrpt_index *idx, int64_t m, int32_t k, int32
     if (L.capq < 1) L.capq = 1;
     // candidate-search work items: chunks of a list, at least 2(k + margin)
     // candidates and 64 (float32) or 32 (bfloat16) each
-    L.chunk = int32_t(std::max<int64_t>(precision == MRPT_PREC_BF16 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
+    L.chunk = int32_t(std::max<int64_t>(precision != MRPT_PREC_FP32 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
     if (opts && opts->chunk > 0) L.chunk = int32_t(std::max<int64_t>(opts->chunk, ks));
     L.ring = (opts && opts->ring > 0) ? std::min<int32_t>(std::max<int32_t>(opts->ring, 2), 16) : 0;
     L.max_items_q = (L.capq + L.chunk - 1) / L.chunk;
@@ -359,18 +360,18 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         return MRPT_ERR_INVALID_ARG;
     }
     const int32_t precision = opts ? opts->precision : MRPT_PREC_FP32;
-    const int32_t margin = (opts && precision == MRPT_PREC_BF16) ? opts->margin : 0;
-    if (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16) {
+    const int32_t margin = (opts && precision != MRPT_PREC_FP32) ? opts->margin : 0;
+    if (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16 && precision != MRPT_PREC_FP8) {
         set_error("mrpt_query: unknown precision");
         return MRPT_ERR_INVALID_ARG;
     }
-    if (precision == MRPT_PREC_BF16) {
-        if (!idx->Xb) {
-            set_error("mrpt_query: bfloat16 distances need mrpt_add_lowp(idx, MRPT_PREC_BF16) first");
+    if (precision != MRPT_PREC_FP32) {
+        if ((precision == MRPT_PREC_BF16 && !idx->Xb) || (precision == MRPT_PREC_FP8 && !idx->X8)) {
+            set_error("mrpt_query: reduced-precision distances need mrpt_add_lowp(idx, precision) first");
             return MRPT_ERR_INVALID_ARG;
         }
         if (opts->path != 0 || margin < 0 || k + margin > MRPT_MAX_K) {
-            set_error("mrpt_query: bfloat16 distances need path 0 and 0 <= margin, k + margin <= " +
+            set_error("mrpt_query: reduced-precision distances need path 0 and 0 <= margin, k + margin <= " +
                       std::to_string(MRPT_MAX_K));
             return MRPT_ERR_INVALID_ARG;
         }
@@ -475,11 +476,11 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
 
 int mrpt_add_lowp(mrpt_index *idx, int32_t precision) {
     clear_error();
-    if (!idx || precision != MRPT_PREC_BF16) {
-        set_error("mrpt_add_lowp: need an index and precision MRPT_PREC_BF16");
+    if (!idx || (precision != MRPT_PREC_BF16 && precision != MRPT_PREC_FP8)) {
+        set_error("mrpt_add_lowp: need an index and precision MRPT_PREC_BF16 or MRPT_PREC_FP8");
         return MRPT_ERR_INVALID_ARG;
     }
-    return make_bf16_copy(idx);
+    return precision == MRPT_PREC_BF16 ? make_bf16_copy(idx) : make_fp8_copy(idx);
 }
 
 int mrpt_query(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v, int32_t *out_ids,
@@ -509,10 +510,12 @@ int mrpt_plan_create(mrpt_index *idx, int64_t m_max, int32_t k, int32_t v,
     const int32_t n_trees = (opts && opts->n_trees > 0) ? opts->n_trees : idx->T;
     const int32_t path = opts ? opts->path : 0;
     const int32_t precision = opts ? opts->precision : MRPT_PREC_FP32;
-    const int32_t margin = (opts && precision == MRPT_PREC_BF16) ? opts->margin : 0;
+    const int32_t margin = (opts && precision != MRPT_PREC_FP32) ? opts->margin : 0;
     if (m_max < 1 || k < 1 || k > MRPT_MAX_K || v < 1 || n_trees > idx->T || v > n_trees ||
-        (path != 0 && path != 1) || (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16) ||
-        (precision == MRPT_PREC_BF16 && (!idx->Xb || path != 0 || margin < 0 || k + margin > MRPT_MAX_K)) ||
+        (path != 0 && path != 1) ||
+        (precision != MRPT_PREC_FP32 && precision != MRPT_PREC_BF16 && precision != MRPT_PREC_FP8) ||
+        (precision == MRPT_PREC_BF16 && !idx->Xb) || (precision == MRPT_PREC_FP8 && !idx->X8) ||
+        (precision != MRPT_PREC_FP32 && (path != 0 || margin < 0 || k + margin > MRPT_MAX_K)) ||
         (opts && (opts->chunk < 0 || opts->ring < 0 || opts->proj || opts->leaf || opts->votes ||
                   opts->n_cand || opts->cand || opts->stage_ms))) {
         set_error("mrpt_plan_create: invalid argument (need m_max >= 1, 1 <= k <= " +

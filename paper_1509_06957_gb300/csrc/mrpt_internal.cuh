@@ -63,6 +63,8 @@ struct mrpt_index {
     float *X = nullptr;          // n x dpad, zero padded
     uint16_t *Xb = nullptr;      // optional bfloat16 copy of X (same stride)
     bool bf16_exact = false;     // every value of X is exactly representable in bfloat16
+    unsigned char *X8 = nullptr; // optional e4m3 copy: row8_bytes per row (values, scale)
+    int32_t row8_bytes = 0;
     int32_t *col_off = nullptr;  // T*l + 1
     int32_t *dim = nullptr;      // nnz
     float *val = nullptr;        // nnz
@@ -156,6 +158,9 @@ int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *
 
 // Fills idx->Xb with X rounded to bfloat16 (allocating it on first use).
 int make_bf16_copy(mrpt_index *idx);
+
+// Fills idx->X8 with X as e4m3 with a per-row scale (allocating it first).
+int make_fp8_copy(mrpt_index *idx);
 
 // Stream-ordered write of a plan's batch record.
 int set_record(QueryRecord *rec, const QueryRecord &r, cudaStream_t s);

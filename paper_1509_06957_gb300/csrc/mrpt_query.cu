@@ -14,6 +14,7 @@
 //                   per-warp sorted top-k in registers; the warps' lists are
 //                   merged by rank (knn(q, k, S) of Algorithm 4).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -400,6 +401,72 @@ __device__ __forceinline__ void smem_rows2_sq_dist(const ROW *r0, const ROW *r1,
     }
     d0 = sa;
     d1 = sb;
+}
+
+// Four e4m3 values (one 32-bit word) widened to float.
+__device__ __forceinline__ float4 e4m3x4_to_float4(uint32_t w) {
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(w & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(w >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Two staged e4m3 rows (each value times its row's scale) against the
+// staged query; step j covers components 4j .. 4j+3.
+__device__ __forceinline__ void smem_rows2_sq_dist_fp8(const uint32_t *r0, const uint32_t *r1,
+                                                       float s0, float s1, const float4 *q4, int nv4,
+                                                       int lane, float &d0, float &d1) {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll 2
+    for (int j = lane; j < nv4; j += 32) {
+        const float4 q = q4[j];
+        const float4 x = e4m3x4_to_float4(r0[j]);
+        const float4 y = e4m3x4_to_float4(r1[j]);
+        float t;
+        t = __fmaf_rn(-s0, x.x, q.x); a0 = __fmaf_rn(t, t, a0);
+        t = __fmaf_rn(-s0, x.y, q.y); a1 = __fmaf_rn(t, t, a1);
+        t = __fmaf_rn(-s0, x.z, q.z); a0 = __fmaf_rn(t, t, a0);
+        t = __fmaf_rn(-s0, x.w, q.w); a1 = __fmaf_rn(t, t, a1);
+        t = __fmaf_rn(-s1, y.x, q.x); b0 = __fmaf_rn(t, t, b0);
+        t = __fmaf_rn(-s1, y.y, q.y); b1 = __fmaf_rn(t, t, b1);
+        t = __fmaf_rn(-s1, y.z, q.z); b0 = __fmaf_rn(t, t, b0);
+        t = __fmaf_rn(-s1, y.w, q.w); b1 = __fmaf_rn(t, t, b1);
+    }
+    float sa = a0 + a1, sb = b0 + b1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    d0 = sa;
+    d1 = sb;
+}
+
+// float32 rows -> e4m3 rows with a per-row scale max|x| / 448 (one warp per
+// row).  Row layout: row_bytes - 16 e4m3 values (zero beyond d), then the
+// float32 scale, then padding.
+__global__ void k_to_fp8(const float *__restrict__ X, int64_t n, int32_t dpad,
+                         unsigned char *__restrict__ Y, int32_t row_bytes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int vals = row_bytes - 16;
+    for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const float *x = X + r * dpad;
+        float mx = 0.f;
+        for (int i = lane; i < dpad; i += 32) mx = fmaxf(mx, fabsf(x[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float scale = mx > 0.f ? mx / 448.0f : 1.0f;
+        const float inv = 1.0f / scale;
+        unsigned char *y = Y + r * row_bytes;
+        for (int i = lane; i < vals; i += 32) {
+            const __nv_fp8_e4m3 v(i < dpad ? x[i] * inv : 0.0f);
+            y[i] = *reinterpret_cast<const unsigned char *>(&v);
+        }
+        if (lane == 0) *reinterpret_cast<float *>(y + vals) = scale;
+        if (lane >= 1 && lane < 13) y[vals + 3 + lane] = 0;
+    }
 }
 
 // float32 rows -> bfloat16 copy (round to nearest even), same row stride;
@@ -932,6 +999,7 @@ struct CandKnnArgs {
     const void *rows;      // rows the distances are computed from (X or its bf16 copy)
     int32_t kfinal;        // neighbours returned (k); a.k holds k + margin when re-ranking
     int32_t rerank;        // re-rank the survivors with float32 rows
+    uint32_t row_bytes;    // bytes of one staged row
     int32_t ring;          // rows staged per warp (k_cand_knn)
     uint32_t *status;
     int32_t dpad;
@@ -1025,7 +1093,8 @@ __global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs 
 constexpr int CR_WARPS = 4;
 constexpr int CR_MAX_RING = 16;
 
-template <int KR, bool BF16>
+// RK: 0 float32 rows, 1 bfloat16 rows, 2 e4m3 rows with a per-row scale.
+template <int KR, int RK>
 __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0) {
     CandKnnArgs a = a0;
     if (a.rec != nullptr) {
@@ -1039,7 +1108,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int S = a.ring;
-    const uint32_t row_bytes = uint32_t(a.dpad) * (BF16 ? 2u : 4u);
+    const uint32_t row_bytes = a.row_bytes;
     unsigned char *wbase = csm + size_t(warp) * (size_t(a.dpad) * 4 + size_t(S) * row_bytes);
     float *qv = reinterpret_cast<float *>(wbase);
     unsigned char *ring = wbase + size_t(a.dpad) * 4;
@@ -1142,7 +1211,15 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
                 inflight &= ~(1u << slot1);
             }
             float dd0, dd1;
-            if (BF16)
+            if (RK == 2) {
+                const unsigned char *p0 = ring + size_t(slot) * row_bytes;
+                const unsigned char *p1 = ring + size_t(two ? slot1 : slot) * row_bytes;
+                const float s0 = *reinterpret_cast<const float *>(p0 + row_bytes - 16);
+                const float s1 = *reinterpret_cast<const float *>(p1 + row_bytes - 16);
+                smem_rows2_sq_dist_fp8(reinterpret_cast<const uint32_t *>(p0),
+                                       reinterpret_cast<const uint32_t *>(p1), s0, s1, q4, nv4, lane,
+                                       dd0, dd1);
+            } else if (RK == 1)
                 smem_rows2_sq_dist<uint2>(reinterpret_cast<const uint2 *>(ring + size_t(slot) * row_bytes),
                                           reinterpret_cast<const uint2 *>(ring + size_t(two ? slot1 : slot) * row_bytes),
                                           q4, nv4, lane, dd0, dd1);
@@ -1199,12 +1276,13 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
                 }
             }
         }
-        if (finish && BF16 && a.rerank) {
+        if (finish && RK != 0 && a.rerank) {
             // re-rank: exact float32 distances of the k + margin survivors,
-            // whose float32 rows stream through the ring two bfloat16 slots
-            // at a time; keep the k smallest
-            const int S2 = S / 2;
-            const uint32_t frow = row_bytes * 2u;
+            // whose float32 rows stream through the ring, SP reduced-precision
+            // slots per float32 row; keep the k smallest
+            const uint32_t frow = uint32_t(a.dpad) * 4u;
+            const int SP = int((frow + row_bytes - 1) / row_bytes);
+            const int S2 = S / SP;
             const unsigned char *Xf = reinterpret_cast<const unsigned char *>(a.X);
             auto sid = [&](int f) -> int32_t {
                 int32_t v = SENTINEL_ID;
@@ -1222,11 +1300,11 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
             auto issue2 = [&](int f, int ss) {
                 const int32_t id2 = sid(f);
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(&bar[2 * ss], frow);
-                    bulk_copy_g2s(ring + size_t(2 * ss) * row_bytes, Xf + size_t(id2) * frow, frow,
-                                  &bar[2 * ss]);
+                    mbar_arrive_expect_tx(&bar[SP * ss], frow);
+                    bulk_copy_g2s(ring + size_t(SP * ss) * row_bytes, Xf + size_t(id2) * frow, frow,
+                                  &bar[SP * ss]);
                 }
-                inflight |= 1u << (2 * ss);
+                inflight |= 1u << (SP * ss);
             };
             const int prime2 = nsurv < S2 ? nsurv : S2;
             for (int f = 0; f < prime2; ++f) issue2(f, f);
@@ -1236,7 +1314,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
             int ss = 0;
             for (int f = 0; f < nsurv; ++f) {
                 const int32_t id2 = sid(f);
-                const int bslot = 2 * ss;
+                const int bslot = SP * ss;
                 if (!__all_sync(0xffffffffu, mbar_wait(&bar[bslot], (parity >> bslot) & 1u))) {
                     failed = true;
                     break;
@@ -1440,17 +1518,27 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     return cudaGetLastError();
 }
 
-template <int KR, bool BF16>
+template <int KR, int RK>
 cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const size_t row_bytes = size_t(idx->dpad) * (BF16 ? 2 : 4);
+    const size_t row_bytes = RK == 2 ? size_t(idx->row8_bytes) : size_t(idx->dpad) * (RK == 1 ? 2 : 4);
+    constexpr bool BF16 = RK != 0;  // reduced-precision rows (staged path only)
     // rows staged per warp: two (one pair in flight) by default -- the
     // kernel hides latency with resident warps rather than ring depth, so
     // the smallest ring (most warps per SM) measured fastest
     int ring = ql.ring > 0 ? ql.ring : 2;
+    // a re-rank streams float32 rows through the ring: it must hold one
+    const bool rerank = RK == 2 || (RK == 1 && !idx->bf16_exact);
+    if (rerank) {
+        const int sp = int((size_t(idx->dpad) * 4 + row_bytes - 1) / row_bytes);
+        ring = std::max(ring, std::min(sp, CR_MAX_RING));
+    }
     const size_t per_warp = size_t(idx->dpad) * 4 + size_t(ring) * row_bytes;
     CandKnnArgs a{};
     a.X = idx->X;
-    a.rows = BF16 ? static_cast<const void *>(idx->Xb) : static_cast<const void *>(idx->X);
+    a.rows = RK == 2   ? static_cast<const void *>(idx->X8)
+             : RK == 1 ? static_cast<const void *>(idx->Xb)
+                       : static_cast<const void *>(idx->X);
+    a.row_bytes = uint32_t(row_bytes);
     a.kfinal = ql.k;
     a.dpad = idx->dpad;
     a.Q = ql.Q;
@@ -1461,7 +1549,7 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.ncand = ql.ncand;
     // a lossless bfloat16 copy gives float32 distances up to summation
     // order: no survivors beyond k and no re-rank are needed
-    a.rerank = (BF16 && !idx->bf16_exact) ? 1 : 0;
+    a.rerank = rerank ? 1 : 0;
     a.k = ql.k + (a.rerank ? ql.margin : 0);
     a.out_ids = ql.out_ids;
     a.out_dists = ql.out_dists;
@@ -1482,14 +1570,14 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     if (e != cudaSuccess) return e;
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
-        e = cudaFuncSetAttribute(k_cand_knn<KR, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        e = cudaFuncSetAttribute(k_cand_knn<KR, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR, BF16>, CR_WARPS * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR, RK>, CR_WARPS * 32, smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((ql.m + CR_WARPS - 1) / CR_WARPS, int64_t(sms) * std::max(per_sm, 1)));
-        k_cand_knn<KR, BF16><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
+        k_cand_knn<KR, RK><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
         return cudaGetLastError();
     }
     // float32 rows too long to stage: register path
@@ -1564,21 +1652,31 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
             // survivors kept for the re-rank (none beyond k when it is skipped)
             const int krs = (ql.k + (idx->bf16_exact ? 0 : ql.margin) + 31) / 32;
             if (krs <= 1)
-                e = launch_cand_knn<1, true>(idx, ql, s);
+                e = launch_cand_knn<1, 1>(idx, ql, s);
             else if (krs <= 2)
-                e = launch_cand_knn<2, true>(idx, ql, s);
+                e = launch_cand_knn<2, 1>(idx, ql, s);
             else if (krs <= 4)
-                e = launch_cand_knn<4, true>(idx, ql, s);
+                e = launch_cand_knn<4, 1>(idx, ql, s);
             else
-                e = launch_cand_knn<8, true>(idx, ql, s);
+                e = launch_cand_knn<8, 1>(idx, ql, s);
+        } else if (ql.precision == 2) {
+            const int krs = (ql.k + ql.margin + 31) / 32;
+            if (krs <= 1)
+                e = launch_cand_knn<1, 2>(idx, ql, s);
+            else if (krs <= 2)
+                e = launch_cand_knn<2, 2>(idx, ql, s);
+            else if (krs <= 4)
+                e = launch_cand_knn<4, 2>(idx, ql, s);
+            else
+                e = launch_cand_knn<8, 2>(idx, ql, s);
         } else if (kr <= 1) {
-            e = launch_cand_knn<1, false>(idx, ql, s);
+            e = launch_cand_knn<1, 0>(idx, ql, s);
         } else if (kr <= 2) {
-            e = launch_cand_knn<2, false>(idx, ql, s);
+            e = launch_cand_knn<2, 0>(idx, ql, s);
         } else if (kr <= 4) {
-            e = launch_cand_knn<4, false>(idx, ql, s);
+            e = launch_cand_knn<4, 0>(idx, ql, s);
         } else {
-            e = launch_cand_knn<8, false>(idx, ql, s);
+            e = launch_cand_knn<8, 0>(idx, ql, s);
         }
         if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
         if (kr <= 1)
@@ -1675,6 +1773,25 @@ __global__ void k_set_record(QueryRecord *rec, QueryRecord r) { *rec = r; }
 int set_record(QueryRecord *rec, const QueryRecord &r, cudaStream_t s) {
     k_set_record<<<1, 1, 0, s>>>(rec, r);
     MRPT_CUDA_TRY(cudaGetLastError());
+    return MRPT_OK;
+}
+
+}  // namespace mrpt
+
+namespace mrpt {
+
+int make_fp8_copy(mrpt_index *idx) {
+    idx->row8_bytes = ((idx->dpad + 15) & ~15) + 16;
+    if (!idx->X8) {
+        const size_t bytes = size_t(idx->n) * size_t(idx->row8_bytes);
+        int rc = dev_alloc(reinterpret_cast<void **>(&idx->X8), bytes, "e4m3 copy");
+        if (rc) return rc;
+        idx->device_bytes += int64_t(bytes);
+    }
+    const int blocks = int(std::min<int64_t>((idx->n * 32 + 255) / 256, 152 * 16));
+    k_to_fp8<<<blocks, 256, 0, idx->stream>>>(idx->X, idx->n, idx->dpad, idx->X8, idx->row8_bytes);
+    MRPT_CUDA_TRY(cudaGetLastError());
+    MRPT_CUDA_TRY(cudaStreamSynchronize(idx->stream));
     return MRPT_OK;
 }
 
