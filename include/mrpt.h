@@ -180,6 +180,18 @@ int mrpt_plan_run(mrpt_plan *plan, const float *Q, int64_t m, int32_t *out_ids,
                   float *out_dists);
 int mrpt_plan_free(mrpt_plan *plan);
 
+/*
+ * mrpt_save / mrpt_load -- the index in the compact form that a median split
+ * allows (Sec. II-A): header, the random matrix (compressed columns), one
+ * split value per inner node, the leaf lists and the data; leaf boundaries
+ * are not stored (they follow from n and l).  Host byte order.  A loaded index
+ * answers queries exactly as the saved one; reduced-precision copies are not
+ * saved (call mrpt_add_lowp again).  Synchronous.
+ * Errors: INVALID_ARG (path, bad or truncated file), OOM, CUDA.
+ */
+int mrpt_save(const mrpt_index *idx, const char *path);
+int mrpt_load(const char *path, mrpt_index **out);
+
 /* Release the index and everything it owns.  NULL is accepted. */
 int mrpt_free(mrpt_index *idx);
 

@@ -51,7 +51,7 @@ ABI_SYMBOLS = (
     "mrpt_build", "mrpt_query", "mrpt_query_ex", "mrpt_free", "mrpt_last_error",
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
     "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
-    "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free",
+    "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free", "mrpt_save", "mrpt_load",
 )
 MRPT_PREC_FP32 = 0
 MRPT_PREC_BF16 = 1
@@ -148,6 +148,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_plan_run.argtypes = [vp, vp, i64, vp, vp]
         lib.mrpt_plan_free.restype = ctypes.c_int
         lib.mrpt_plan_free.argtypes = [vp]
+        lib.mrpt_save.restype = ctypes.c_int
+        lib.mrpt_save.argtypes = [vp, ctypes.c_char_p]
+        lib.mrpt_load.restype = ctypes.c_int
+        lib.mrpt_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
         lib.mrpt_add_lowp.restype = ctypes.c_int
         lib.mrpt_add_lowp.argtypes = [vp, i32]
         lib.mrpt_query_noalloc.restype = ctypes.c_int
@@ -269,6 +273,18 @@ def mrpt_add_lowp(index: Index, precision: int = MRPT_PREC_BF16) -> None:
     """Add a bfloat16 (MRPT_PREC_BF16) or e4m3 + per-row scale
     (MRPT_PREC_FP8) copy of the data for reduced-precision distances."""
     _check(load_library().mrpt_add_lowp(index.handle, int(precision)))
+
+
+def mrpt_save(index: Index, path: str) -> None:
+    """Write the index (random matrix, splits, leaves, data) to `path`."""
+    _check(load_library().mrpt_save(index.handle, os.fsencode(path)))
+
+
+def mrpt_load(path: str) -> Index:
+    """Read an index written by mrpt_save onto the current device."""
+    h = ctypes.c_void_p()
+    _check(load_library().mrpt_load(os.fsencode(path), ctypes.byref(h)))
+    return Index(h)
 
 
 def mrpt_free(index: Index) -> None:

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -638,6 +639,187 @@ int mrpt_plan_run(mrpt_plan *plan, const float *Q, int64_t m, int32_t *out_ids, 
     if (!ids_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_ids, plan->ids_stage, ob, cudaMemcpyDeviceToHost, s));
     if (!dists_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_dists, plan->dists_stage, ob, cudaMemcpyDeviceToHost, s));
     if (any_host) return mrpt_sync(idx);
+    return MRPT_OK;
+}
+
+// ---- save / load: "MRPTIDX1", header, R (compressed columns), split
+// values, leaf lists, data.  Little-endian, as the host writes it.
+namespace {
+struct FileHeader {
+    char magic[8];
+    int64_t n;
+    int32_t d, T, l;
+    float density;
+    uint64_t seed;
+    int64_t nnz;
+};
+
+int write_all(FILE *f, const void *p, size_t bytes) { return fwrite(p, 1, bytes, f) == bytes ? 0 : -1; }
+int read_all(FILE *f, void *p, size_t bytes) { return fread(p, 1, bytes, f) == bytes ? 0 : -1; }
+}  // namespace
+
+int mrpt_save(const mrpt_index *idx, const char *path) {
+    clear_error();
+    if (!idx || !path) {
+        set_error("mrpt_save: NULL argument");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    MRPT_CUDA_TRY(cudaStreamSynchronize(idx->stream));
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        set_error(std::string("mrpt_save: cannot open ") + path);
+        return MRPT_ERR_INVALID_ARG;
+    }
+    FileHeader h{};
+    memcpy(h.magic, "MRPTIDX1", 8);
+    h.n = idx->n;
+    h.d = idx->d;
+    h.T = idx->T;
+    h.l = idx->l;
+    h.density = idx->density;
+    h.seed = idx->seed;
+    h.nnz = idx->nnz;
+    const size_t sb = size_t(idx->T) * size_t(idx->L - 1) * 4;
+    const size_t ib = size_t(idx->T) * size_t(idx->n) * 4;
+    const size_t xb = size_t(idx->n) * size_t(idx->d) * 4;
+    std::string err;
+    void *host = malloc(std::max(std::max(sb, ib), std::max(xb, size_t(1))));
+    int bad = host ? 0 : -1;
+    if (!bad) bad = write_all(f, &h, sizeof(h));
+    if (!bad) bad = write_all(f, idx->h_col_off.data(), idx->h_col_off.size() * 4);
+    if (!bad && idx->nnz) bad = write_all(f, idx->h_dim.data(), size_t(idx->nnz) * 4);
+    if (!bad && idx->nnz) bad = write_all(f, idx->h_val.data(), size_t(idx->nnz) * 4);
+    cudaError_t e = cudaSuccess;
+    if (!bad && sb) {
+        e = cudaMemcpy(host, idx->split, sb, cudaMemcpyDeviceToHost);
+        bad = e != cudaSuccess ? -2 : write_all(f, host, sb);
+    }
+    if (!bad) {
+        e = cudaMemcpy(host, idx->leaf_ids, ib, cudaMemcpyDeviceToHost);
+        bad = e != cudaSuccess ? -2 : write_all(f, host, ib);
+    }
+    if (!bad) {
+        e = cudaMemcpy2D(host, size_t(idx->d) * 4, idx->X, size_t(idx->dpad) * 4, size_t(idx->d) * 4,
+                         size_t(idx->n), cudaMemcpyDeviceToHost);
+        bad = e != cudaSuccess ? -2 : write_all(f, host, xb);
+    }
+    free(host);
+    if (fclose(f) != 0 && !bad) bad = -1;
+    if (bad == -2) return cuda_fail(e, "mrpt_save");
+    if (bad) {
+        set_error(host ? "mrpt_save: write failed" : "mrpt_save: host allocation failed");
+        return host ? MRPT_ERR_INVALID_ARG : MRPT_ERR_OOM;
+    }
+    return MRPT_OK;
+}
+
+int mrpt_load(const char *path, mrpt_index **out) {
+    clear_error();
+    if (!path || !out) {
+        set_error("mrpt_load: NULL argument");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        set_error(std::string("mrpt_load: cannot open ") + path);
+        return MRPT_ERR_INVALID_ARG;
+    }
+    FileHeader h{};
+    if (read_all(f, &h, sizeof(h)) || memcmp(h.magic, "MRPTIDX1", 8) != 0 || h.n < 1 || h.d < 1 ||
+        h.d > MRPT_MAX_DIM || h.T < 1 || h.T > MRPT_MAX_TREES || h.l < 0 || h.l > MRPT_MAX_DEPTH ||
+        (int64_t(1) << h.l) > h.n || h.nnz < 0) {
+        fclose(f);
+        set_error("mrpt_load: not an index file or unsupported header");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    mrpt_index *idx = new (std::nothrow) mrpt_index();
+    if (!idx) {
+        fclose(f);
+        set_error("mrpt_load: host allocation failed");
+        return MRPT_ERR_OOM;
+    }
+    cudaGetDevice(&idx->device);
+    idx->n = h.n;
+    idx->d = h.d;
+    idx->dpad = (h.d + 7) & ~7;
+    idx->T = h.T;
+    idx->l = h.l;
+    idx->L = int64_t(1) << h.l;
+    idx->density = h.density;
+    idx->seed = h.seed;
+    idx->nnz = h.nnz;
+    auto fail = [&](int code, const char *msg) {
+        fclose(f);
+        if (msg) set_error(msg);
+        free_index(idx);
+        return code;
+    };
+    idx->h_col_off.resize(size_t(h.T) * h.l + 1);
+    idx->h_dim.resize(size_t(h.nnz));
+    idx->h_val.resize(size_t(h.nnz));
+    if (read_all(f, idx->h_col_off.data(), idx->h_col_off.size() * 4) ||
+        (h.nnz && read_all(f, idx->h_dim.data(), size_t(h.nnz) * 4)) ||
+        (h.nnz && read_all(f, idx->h_val.data(), size_t(h.nnz) * 4)) ||
+        idx->h_col_off.back() != h.nnz)
+        return fail(MRPT_ERR_INVALID_ARG, "mrpt_load: truncated or inconsistent random matrix");
+    for (int32_t x : idx->h_dim)
+        if (x < 0 || x >= h.d) return fail(MRPT_ERR_INVALID_ARG, "mrpt_load: dimension out of range");
+    const size_t cb = idx->h_col_off.size() * 4, nb = size_t(h.nnz) * 4;
+    const size_t sb = size_t(h.T) * size_t(idx->L - 1) * 4;
+    const size_t ib = size_t(h.T) * size_t(h.n) * 4;
+    const size_t xb = size_t(h.n) * size_t(h.d) * 4;
+    int rc;
+    if ((rc = dev_alloc((void **)&idx->col_off, cb, "R column offsets")) ||
+        (rc = dev_alloc((void **)&idx->dim, nb, "R dimensions")) ||
+        (rc = dev_alloc((void **)&idx->val, nb, "R values")) ||
+        (rc = dev_alloc((void **)&idx->split, sb, "split values")) ||
+        (rc = dev_alloc((void **)&idx->leaf_off, size_t(idx->L + 1) * 4, "leaf offsets")) ||
+        (rc = dev_alloc((void **)&idx->leaf_ids, ib, "leaf ids")) ||
+        (rc = dev_alloc((void **)&idx->status, 8 * sizeof(uint32_t), "status words")) ||
+        (rc = dev_alloc((void **)&idx->X, size_t(h.n) * size_t(idx->dpad) * 4, "index data")))
+        return fail(rc, nullptr);
+    idx->device_bytes = int64_t(cb + 2 * nb + sb + size_t(idx->L + 1) * 4 + ib + 32 +
+                                size_t(h.n) * size_t(idx->dpad) * 4);
+    void *host = malloc(std::max(std::max(sb, ib), std::max(xb, size_t(1))));
+    if (!host) return fail(MRPT_ERR_OOM, "mrpt_load: host allocation failed");
+    cudaError_t e = cudaMemset(idx->status, 0, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(idx->col_off, idx->h_col_off.data(), cb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nb) e = cudaMemcpy(idx->dim, idx->h_dim.data(), nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nb) e = cudaMemcpy(idx->val, idx->h_val.data(), nb, cudaMemcpyHostToDevice);
+    bool short_read = false;
+    if (e == cudaSuccess && sb) {
+        short_read = read_all(f, host, sb) != 0;
+        if (!short_read) e = cudaMemcpy(idx->split, host, sb, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && !short_read) {
+        short_read = read_all(f, host, ib) != 0;
+        const int32_t *ids = static_cast<const int32_t *>(host);
+        for (size_t i = 0; !short_read && i < size_t(h.T) * size_t(h.n); ++i)
+            if (ids[i] < 0 || ids[i] >= h.n) short_read = true;
+        if (!short_read) e = cudaMemcpy(idx->leaf_ids, host, ib, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && !short_read) {
+        short_read = read_all(f, host, xb) != 0;
+        if (!short_read) e = cudaMemset(idx->X, 0, size_t(h.n) * size_t(idx->dpad) * 4);
+        if (!short_read && e == cudaSuccess)
+            e = cudaMemcpy2D(idx->X, size_t(idx->dpad) * 4, host, size_t(h.d) * 4, size_t(h.d) * 4,
+                             size_t(h.n), cudaMemcpyHostToDevice);
+    }
+    free(host);
+    if (e != cudaSuccess) {
+        const int code = cuda_fail(e, "mrpt_load");
+        fclose(f);
+        free_index(idx);
+        return code;
+    }
+    if (short_read) return fail(MRPT_ERR_INVALID_ARG, "mrpt_load: truncated file or leaf id out of range");
+    fclose(f);
+    if ((rc = compute_leaf_offsets(idx))) {
+        free_index(idx);
+        return rc;
+    }
+    *out = idx;
     return MRPT_OK;
 }
 

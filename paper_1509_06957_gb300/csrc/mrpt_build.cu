@@ -447,4 +447,14 @@ int grow_trees_device(mrpt_index *idx) {
     return MRPT_OK;
 }
 
+// Leaf offsets of a loaded index (they depend only on n and l).
+int compute_leaf_offsets(mrpt_index *idx) {
+    const int blocks = int(std::min<int64_t>((idx->L + 1 + 255) / 256, 152 * 32));
+    k_leaf_offsets<<<blocks, 256, 0, idx->stream>>>(idx->leaf_off, idx->n, idx->l);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "k_leaf_offsets");
+    return MRPT_OK;
+}
+
 }  // namespace mrpt

@@ -101,6 +101,9 @@ void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint
 // idx->leaf_off and idx->leaf_ids.  X, R must already be on the device.
 int grow_trees_device(mrpt_index *idx);
 
+// Leaf offsets (identical for every tree) of an index whose trees were loaded.
+int compute_leaf_offsets(mrpt_index *idx);
+
 // Sets *nonfinite when the n x dpad matrix X holds NaN/Inf.
 int check_finite(const float *X, int64_t rows, int32_t stride, int32_t cols, cudaStream_t s,
                  bool *nonfinite);

@@ -1,0 +1,74 @@
+"""GPU: index save/load, the paper's fully specified "Random" workload
+(unit-length N(0, I) vectors, d = 4096, Sec. IV-A) and the dense
+(a = 1, classic RP tree) ablation, each against the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import check_index_parity, check_results, oracle_sets
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_06957_gb300 as m
+    m.load_library()
+    return m
+
+
+def _check(mr, X, Q, T, l, k, v, density, seed, idx=None):
+    own = idx is None
+    if own:
+        idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, density, seed)
+    ref = oracle.grow_trees(X, T, l, density, seed)
+    check_index_parity(idx, mr, ref)
+    gi, gd = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v)
+    torch.cuda.synchronize()
+    oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, want_internals=True)
+    check_results(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, oracle_sets(ref, oleaf, v))
+    if own:
+        idx.close()
+
+
+def test_save_load_roundtrip(mr, tmp_path):
+    X, Q = workloads.gaussian_mixture(3000, 20, 30, n_centres=9, seed=3)
+    idx = mr.mrpt_build(X, 7, 5, 0.3, 12)
+    path = str(tmp_path / "index.mrpt")
+    mr.mrpt_save(idx, path)
+    idx2 = mr.mrpt_load(path)
+    for what in ("R_COL_OFF", "R_DIM", "R_VAL", "SPLIT", "LEAF_OFF", "LEAF_IDS", "DATA"):
+        assert np.array_equal(mr.mrpt_export(idx, what), mr.mrpt_export(idx2, what)), what
+    a = mr.mrpt_query(idx, Q, 10, 2)
+    b = mr.mrpt_query(idx2, Q, 10, 2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    _check(mr, X, Q, 7, 5, 10, 2, 0.3, 12, idx=idx2)
+    # damaged files are refused
+    blob = open(path, "rb").read()
+    open(path, "wb").write(blob[: len(blob) // 2])
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_load(path)
+    assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+    open(path, "wb").write(b"NOTANIDX" + blob[8:])
+    with pytest.raises(mr.MRPTError):
+        mr.mrpt_load(path)
+    idx.close()
+    idx2.close()
+
+
+def test_random_unit_vectors_d4096(mr):
+    """The paper's "Random" set shape: unit-length N(0, I) vectors, d = 4096."""
+    X, Q = workloads.unit_gaussian(4000, 4096, 12, seed=5)
+    _check(mr, X, Q, 6, 5, 10, 2, float(np.float32(4096 ** -0.5)), 1)
+
+
+def test_dense_classic_rp_trees(mr):
+    """a = 1: classic dense RP trees with one vector per level."""
+    X, Q = workloads.gaussian_mixture(2000, 48, 20, n_centres=10, seed=6)
+    _check(mr, X, Q, 5, 4, 10, 2, 1.0, 4)
