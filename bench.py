@@ -234,9 +234,12 @@ def run_gpu(args):
     mr.mrpt_add_lowp(index, mr.MRPT_PREC_BF16)
     mr.mrpt_add_lowp(index, mr.MRPT_PREC_FP8)
 
+    knobs = dict(chunk=0, ring=0)
+
     def query(T_use, v, stage=None, prec=0, margin=0):
         mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, out_ids=ids, out_dists=dists,
-                         stage_ms=stage, path=args.path, precision=prec, margin=margin)
+                         stage_ms=stage, path=args.path, precision=prec, margin=margin,
+                         chunk=knobs["chunk"], ring=knobs["ring"])
 
     # ---- sweep (T, v): fastest with recall >= target (tie-aware), unless
     # the operating point is given
@@ -264,6 +267,12 @@ def run_gpu(args):
     prec, margin = ("fp32", "bf16", "fp8").index(best["precision"]), best["margin"]
     ok32 = [s for s in ok if s["precision"] == "fp32"]
     best32 = min(ok32, key=lambda s: s["ms"]) if ok32 else None
+
+    # ---- launch knobs (work-item chunk, staged rows, path) for that setting
+    from paper_1509_06957_gb300 import autotune
+    knobs = autotune.tune_kernels(index, Q, k, v, T_use, prec, margin, reps=3)["best"] \
+        if args.path == 0 else dict(path=1, chunk=0, ring=0, ms=None)
+    args.path = knobs["path"]
 
     # ---- mean |S| at the operating point (untimed debug pass)
     _, _, dbg = mr.mrpt_query_ex(index, Q[:2000], k, v, n_trees=T_use, debug=True, cand_cap=1)
@@ -296,7 +305,7 @@ def run_gpu(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec, margin)
+        e2e = run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec, margin, knobs)
 
     # ---- rooflines: voting (leaf ids, L2-resident) and candidate search
     # (candidate rows); "roofline" reports the kernel that takes longer
@@ -361,6 +370,7 @@ def run_gpu(args):
             "config": {"workload": W["name"], "n": n, "d": d, "queries_per_step": m, "k": k,
                        "depth": l, "T": T_use, "v": v, "density": "1/sqrt(d)",
                        "precision": ("fp32", "bf16", "fp8")[prec], "rerank_margin": margin,
+                       "tuned_knobs": knobs,
                        "fp32_best": best32,
                        "recall_at_10": round(recall_ta, 4),
                        "recall_at_10_strict": round(recall_strict, 4),
@@ -386,7 +396,8 @@ def run_gpu(args):
     return out
 
 
-def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec=0, margin=0):
+def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec=0, margin=0, knobs=None):
+    knobs = knobs or {}
     """The same metric through the public call with pinned host buffers:
     every step copies the queries in and the results out."""
     m, d = Q.shape
@@ -395,7 +406,8 @@ def run_e2e(mr, index, Q, k, v, T_use, flush, args, world, torch, prec=0, margin
     dists_h = torch.empty((m, k), dtype=torch.float32).pin_memory().numpy()
     def call():
         mr.mrpt_query_ex(index, Qh, k, v, n_trees=T_use, out_ids=ids_h, out_dists=dists_h,
-                         precision=prec, margin=margin)
+                         precision=prec, margin=margin, path=args.path, chunk=knobs.get("chunk", 0),
+                         ring=knobs.get("ring", 0))
     call()
     el = 0.0
     for _ in range(args.steps):
@@ -518,11 +530,16 @@ def cpu_baseline(X, Q, T, v, k, l, target_s=15.0):
     per_q = (time.perf_counter() - t0) / len(probe)
     ns = int(min(len(Q), max(len(probe), target_s / max(per_q, 1e-6))))
     sample = Q[:ns]
-    t0 = time.perf_counter()
-    oracle.query(ref, sample, k, v, mode=1, nthreads=threads)
-    el = time.perf_counter() - t0
-    return {"value": round(ns / el, 2), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {ns} of the {len(Q)} queries, T={T}, v={v}, float32 distances, "
+    # repeat the sample (bounded) until about target_s of work has been timed
+    el, done, reps = 0.0, 0, 0
+    while el < target_s and reps < 64:
+        t0 = time.perf_counter()
+        oracle.query(ref, sample, k, v, mode=1, nthreads=threads)
+        el += time.perf_counter() - t0
+        done += ns
+        reps += 1
+    return {"value": round(done / el, 2), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {ns} of the {len(Q)} queries x{reps}, T={T}, v={v}, float32 distances, "
                       f"{el:.1f} s"}
 
 
