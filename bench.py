@@ -494,6 +494,41 @@ def run_stream(args):
     return out
 
 
+def run_build(args):
+    """Index build time (Algorithms 1-2) for the 1M-point shapes, data
+    already on the device: 1M x 128 (T = 100, l = 12) and 1M x 960
+    (T = 200, l = 10).  Each build is timed around the synchronous
+    mrpt_build call (host-visible wall time, device-resident input)."""
+    import torch
+    import paper_1509_06957_gb300 as mr
+    dev = torch.device("cuda", 0)
+    rows = []
+    shapes = [("lognormal-int 1000000x128", workloads.lognormal_int, 128, 100, 12),
+              ("latent-factor 1000000x960", workloads.latent_factor, 960, 200, 10)]
+    for name, gen, d, T, l in shapes[: args.build_shapes]:
+        X_np, _ = gen(1_000_000, d, 1, seed=0)
+        X = torch.from_numpy(X_np).to(dev)
+        del X_np
+        times = []
+        for rep in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            idx = mr.mrpt_build(X, T, l, 0.0, seed=rep)
+            el = time.perf_counter() - t0
+            idx.close()
+            if rep >= args.warmup:
+                times.append(el)
+        flops = 2.0 * 1_000_000 * T * l * (d ** 0.5)   # projections: a d nonzeros per vector
+        rows.append({"workload": name, "T": T, "depth": l, "build_s_median": round(float(np.median(times)), 4),
+                     "build_s_min": round(min(times), 4), "projection_gflop": round(flops / 1e9, 1)})
+        del X
+        torch.cuda.empty_cache()
+    out = {"metric": "index build seconds (all trees, data on the device)", "value": rows[-1]["build_s_median"],
+           "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "builds": rows}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 # ------------------------------------------------------- CPU (oracle) -----
 
 def _oracle_index(X, T, l, seed):
@@ -594,7 +629,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["batch", "stream"], default="batch",
+    ap.add_argument("--build-shapes", type=int, default=2, help="build workload: how many shapes")
+    ap.add_argument("--workload", choices=["batch", "stream", "build"], default="batch",
                     help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
     ap.add_argument("--stream-queries", type=int, default=100000)
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp8"], default="auto",
@@ -612,6 +648,8 @@ def main():
         run_reference(args)
     elif args.workload == "stream":
         run_stream(args)
+    elif args.workload == "build":
+        run_build(args)
     else:
         run_gpu(args)
 

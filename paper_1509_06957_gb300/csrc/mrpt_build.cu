@@ -114,7 +114,7 @@ int check_finite(const float *X, int64_t rows, int32_t stride, int32_t cols, cud
 // nonzeros in ascending dimension from +0.0f.  Output is column-major,
 // Pcm[c * n + x], so that a node's keys for one level are one column.
 template <int RB>
-__global__ void __launch_bounds__(256) k_project_build(
+__global__ void __launch_bounds__(1024) k_project_build(
     const float *__restrict__ X, int64_t n, int32_t dpad, int32_t d,
     const int32_t *__restrict__ col_off, const int32_t *__restrict__ dim,
     const float *__restrict__ val, int32_t ncols, float *__restrict__ Pcm) {
@@ -186,7 +186,7 @@ __device__ __forceinline__ void node_segment(int64_t n, int level, int64_t b, in
 // composite key (ordered projection << 32 | id) by an 8-bit radix select,
 // record its projection as the node's split, and stably partition members
 // with composite <= pivot to the left part out[0..ceil(c/2)).
-__global__ void __launch_bounds__(256) k_split_level(
+__global__ void __launch_bounds__(1024) k_split_level(
     const float *__restrict__ Pcm, int64_t n, int32_t l, int32_t level,
     const int32_t *__restrict__ perm_in, int32_t *__restrict__ perm_out,
     float *__restrict__ split, int64_t L) {
@@ -373,8 +373,10 @@ cudaError_t launch_project(const mrpt_index *idx, float *Pcm, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_project_build<RB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
+    // 32 warps per block: the staged rows allow one or two blocks per SM,
+    // and the fmaf chains are latency-bound, so warps are what hides them
     const int64_t blocks = (idx->n + RB - 1) / RB;
-    k_project_build<RB><<<dim3(unsigned(blocks)), 256, smem, s>>>(
+    k_project_build<RB><<<dim3(unsigned(blocks)), 1024, smem, s>>>(
         idx->X, idx->n, idx->dpad, idx->d, idx->col_off, idx->dim, idx->val, idx->T * idx->l,
         Pcm);
     return cudaGetLastError();
@@ -422,8 +424,10 @@ int grow_trees_device(mrpt_index *idx) {
         }
         for (int32_t j = 0; j < l && e == cudaSuccess; ++j) {
             const int64_t blocks = int64_t(T) << j;
-            k_split_level<<<dim3(unsigned(blocks)), 256, 0, s>>>(Pcm, n, l, j, perm_a, perm_b,
-                                                               idx->split, L);
+            // large nodes (few blocks) get 1,024 threads, small ones 256
+            const int threads = (n >> j) >= 16384 ? 1024 : 256;
+            k_split_level<<<dim3(unsigned(blocks)), threads, 0, s>>>(Pcm, n, l, j, perm_a, perm_b,
+                                                                   idx->split, L);
             e = cudaGetLastError();
             std::swap(perm_a, perm_b);
         }
