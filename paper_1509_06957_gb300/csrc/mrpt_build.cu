@@ -4,8 +4,8 @@
 //                                      (Sec. II-B, II-C)
 //   2. k_project_build                 P = XR for all n points and T*l
 //                                      vectors (Algorithm 1), column-major
-//   3. k_split_level (x l)             level-synchronous median split of
-//                                      every node of every tree (Algorithm 2,
+//   3. k_gather_keys + k_split_level   level-synchronous median split of
+//      (x l)                           every node of every tree (Algorithm 2,
 //                                      order-based median of Sec. II-A)
 //   4. k_leaf_offsets                  leaf boundaries (identical per tree)
 //
@@ -186,8 +186,23 @@ __device__ __forceinline__ void node_segment(int64_t n, int level, int64_t b, in
 // composite key (ordered projection << 32 | id) by an 8-bit radix select,
 // record its projection as the node's split, and stably partition members
 // with composite <= pivot to the left part out[0..ceil(c/2)).
+// The level's keys in permutation order: okeys[t n + i] = ordered bits of
+// tree t's level projection of point perm[t n + i].  One gather per level,
+// after which every pass of the split streams contiguous memory.
+__global__ void k_gather_keys(const float *__restrict__ Pcm, int64_t n, int32_t l, int32_t level,
+                              int32_t T, const int32_t *__restrict__ perm,
+                              uint32_t *__restrict__ okeys) {
+    const int64_t total = n * T;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = i / n;
+        okeys[i] = ordered_bits(__ldg(Pcm + (t * l + level) * n + perm[i]));
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_split_level(
-    const float *__restrict__ Pcm, int64_t n, int32_t l, int32_t level,
+    const float *__restrict__ Pcm, const uint32_t *__restrict__ okeys, int64_t n, int32_t l,
+    int32_t level,
     const int32_t *__restrict__ perm_in, int32_t *__restrict__ perm_out,
     float *__restrict__ split, int64_t L) {
     __shared__ uint32_t hist[256];
@@ -202,7 +217,8 @@ __global__ void __launch_bounds__(1024) k_split_level(
     const int64_t b = seg - t * nodes;
     int64_t off, c;
     node_segment(n, level, b, off, c);
-    const float *key = Pcm + (t * l + level) * n;
+    (void)Pcm;
+    const uint32_t *okey = okeys + t * n + off;
     const int32_t *in = perm_in + t * n + off;
     int32_t *out = perm_out + t * n + off;
     const int tid = threadIdx.x;
@@ -212,8 +228,7 @@ __global__ void __launch_bounds__(1024) k_split_level(
     const int nwarps = bd >> 5;
 
     auto composite = [&](int64_t i) -> uint64_t {
-        const int32_t id = in[i];
-        return (uint64_t(ordered_bits(key[id])) << 32) | uint32_t(id);
+        return (uint64_t(okey[i]) << 32) | uint32_t(in[i]);
     };
 
     // ---- radix select of rank r (0-based)
@@ -298,7 +313,7 @@ __global__ void __launch_bounds__(1024) k_split_level(
         bool left = false;
         if (valid) {
             id = in[i];
-            const uint64_t K = (uint64_t(ordered_bits(key[id])) << 32) | uint32_t(id);
+            const uint64_t K = (uint64_t(okey[i]) << 32) | uint32_t(id);
             left = K <= pivot;
         }
         const unsigned lm = __ballot_sync(0xffffffffu, valid && left);
@@ -413,6 +428,13 @@ int grow_trees_device(mrpt_index *idx) {
             cudaFree(Pcm);
             return rc;
         }
+        uint32_t *okeys = nullptr;
+        if ((rc = dev_alloc((void **)&okeys, perm_bytes, "level keys"))) {
+            cudaFree(perm_a);
+            cudaFree(perm_b);
+            cudaFree(Pcm);
+            return rc;
+        }
         cudaError_t e = cudaSuccess;
         switch (pick_rows_per_block(idx->d)) {
             case 32: e = launch_project<32>(idx, Pcm, s); break;
@@ -422,16 +444,19 @@ int grow_trees_device(mrpt_index *idx) {
             case 2: e = launch_project<2>(idx, Pcm, s); break;
             default: e = launch_project<1>(idx, Pcm, s); break;
         }
+        const int gblocks = int(std::min<int64_t>((int64_t(T) * n + 255) / 256, 152 * 32));
         for (int32_t j = 0; j < l && e == cudaSuccess; ++j) {
+            k_gather_keys<<<gblocks, 256, 0, s>>>(Pcm, n, l, j, T, perm_a, okeys);
             const int64_t blocks = int64_t(T) << j;
             // large nodes (few blocks) get 1,024 threads, small ones 256
             const int threads = (n >> j) >= 16384 ? 1024 : 256;
-            k_split_level<<<dim3(unsigned(blocks)), threads, 0, s>>>(Pcm, n, l, j, perm_a, perm_b,
-                                                                   idx->split, L);
+            k_split_level<<<dim3(unsigned(blocks)), threads, 0, s>>>(Pcm, okeys, n, l, j, perm_a,
+                                                                   perm_b, idx->split, L);
             e = cudaGetLastError();
             std::swap(perm_a, perm_b);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(okeys);
         cudaFree(Pcm);
         cudaFree(perm_b);
         if (e != cudaSuccess) {
