@@ -82,12 +82,49 @@ void Scratch::release() {
     bytes = 0;
 }
 
+// The routing kernel reads the nonzeros of R as (dimension, value bits)
+// pairs, two per 16-byte load: every column starts at an even pair index (a
+// column of odd length leaves one unused pair after it), and rcol[c] holds
+// (first pair, count) of column c.  The arithmetic order is unchanged.
+static int upload_route_pairs(mrpt_index *idx) {
+    const int64_t ncols = int64_t(idx->h_col_off.size()) - 1;
+    std::vector<int2> rcol(size_t(ncols > 0 ? ncols : 0));
+    int64_t total = 0;
+    for (int64_t c = 0; c < ncols; ++c) {
+        const int32_t cnt = idx->h_col_off[size_t(c) + 1] - idx->h_col_off[size_t(c)];
+        rcol[size_t(c)] = make_int2(int32_t(total), cnt);
+        total += (cnt + 1) & ~1;
+    }
+    const size_t bytes = size_t(total > 0 ? total : 2) * sizeof(int2);
+    const size_t cbytes = size_t(ncols > 0 ? ncols : 1) * sizeof(int2);
+    int rc = dev_alloc((void **)&idx->dv, bytes, "R routing pairs");
+    if (!rc) rc = dev_alloc((void **)&idx->rcol, cbytes, "R routing columns");
+    if (rc) return rc;
+    idx->device_bytes += int64_t(bytes + cbytes);
+    std::vector<int2> h(bytes / sizeof(int2), make_int2(0, 0));
+    for (int64_t c = 0; c < ncols; ++c) {
+        const int32_t e0 = idx->h_col_off[size_t(c)];
+        for (int32_t k = 0; k < rcol[size_t(c)].y; ++k) {
+            int32_t bits;
+            memcpy(&bits, &idx->h_val[size_t(e0 + k)], sizeof(bits));
+            h[size_t(rcol[size_t(c)].x + k)] = make_int2(idx->h_dim[size_t(e0 + k)], bits);
+        }
+    }
+    cudaError_t e = cudaMemcpy(idx->dv, h.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ncols > 0)
+        e = cudaMemcpy(idx->rcol, rcol.data(), cbytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading R routing pairs");
+    return MRPT_OK;
+}
+
 static void free_index(mrpt_index *idx) {
     if (!idx) return;
     cudaFree(idx->X);
     cudaFree(idx->col_off);
     cudaFree(idx->dim);
     cudaFree(idx->val);
+    cudaFree(idx->dv);
+    cudaFree(idx->rcol);
     cudaFree(idx->split);
     cudaFree(idx->leaf_off);
     cudaFree(idx->leaf_ids);
@@ -260,6 +297,7 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
             e = cudaMemcpy(idx->val, idx->h_val.data(), nbytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: uploading R"));
     }
+    if ((rc = upload_route_pairs(idx))) return fail(rc);
 
     // ---- trees (Algorithm 2)
     const size_t sbytes = size_t(T) * size_t(idx->L - 1) * sizeof(float);
@@ -775,7 +813,7 @@ int mrpt_load(const char *path, mrpt_index **out) {
         (rc = dev_alloc((void **)&idx->val, nb, "R values")) ||
         (rc = dev_alloc((void **)&idx->split, sb, "split values")) ||
         (rc = dev_alloc((void **)&idx->leaf_off, size_t(idx->L + 1) * 4, "leaf offsets")) ||
-        (rc = dev_alloc((void **)&idx->leaf_ids, ib, "leaf ids")) ||
+        (rc = dev_alloc((void **)&idx->leaf_ids, ib + 16, "leaf ids")) ||
         (rc = dev_alloc((void **)&idx->status, 8 * sizeof(uint32_t), "status words")) ||
         (rc = dev_alloc((void **)&idx->X, size_t(h.n) * size_t(idx->dpad) * 4, "index data")))
         return fail(rc, nullptr);
@@ -815,7 +853,7 @@ int mrpt_load(const char *path, mrpt_index **out) {
     }
     if (short_read) return fail(MRPT_ERR_INVALID_ARG, "mrpt_load: truncated file or leaf id out of range");
     fclose(f);
-    if ((rc = compute_leaf_offsets(idx))) {
+    if ((rc = compute_leaf_offsets(idx)) || (rc = upload_route_pairs(idx))) {
         free_index(idx);
         return rc;
     }

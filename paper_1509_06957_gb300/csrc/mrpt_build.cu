@@ -407,7 +407,9 @@ int grow_trees_device(mrpt_index *idx) {
     int32_t *perm_a = nullptr, *perm_b = nullptr;
     float *Pcm = nullptr;
     const size_t perm_bytes = size_t(T) * size_t(n) * sizeof(int32_t);
-    if ((rc = dev_alloc((void **)&perm_a, perm_bytes, "tree permutation"))) return rc;
+    // the leaf array is read in aligned 16-byte groups: 4 spare entries
+    const size_t perm_alloc = perm_bytes + 4 * sizeof(int32_t);
+    if ((rc = dev_alloc((void **)&perm_a, perm_alloc, "tree permutation"))) return rc;
     {
         const int blocks = int(std::min<int64_t>((int64_t(T) * n + 255) / 256, 152 * 32));
         k_iota_trees<<<blocks, 256, 0, s>>>(perm_a, n, T);
@@ -423,7 +425,7 @@ int grow_trees_device(mrpt_index *idx) {
             cudaFree(perm_a);
             return rc;
         }
-        if ((rc = dev_alloc((void **)&perm_b, perm_bytes, "tree permutation"))) {
+        if ((rc = dev_alloc((void **)&perm_b, perm_alloc, "tree permutation"))) {
             cudaFree(perm_a);
             cudaFree(Pcm);
             return rc;

@@ -68,6 +68,8 @@ struct mrpt_index {
     int32_t *col_off = nullptr;  // T*l + 1
     int32_t *dim = nullptr;      // nnz
     float *val = nullptr;        // nnz
+    int2 *dv = nullptr;          // (dimension, value bits) of the nonzeros, columns at even pairs
+    int2 *rcol = nullptr;        // T*l: (first pair in dv, count) of each column
     float *split = nullptr;      // T x (L-1)
     int32_t *leaf_off = nullptr; // L + 1 (identical for every tree)
     int32_t *leaf_ids = nullptr; // T x n

@@ -32,7 +32,7 @@ namespace mrpt {
 // (query tile, group of ROUTE_TREES_PER_ITEM trees); a persistent block
 // takes a contiguous range of items, so it stages a query tile once and
 // walks its tree groups.  All lanes that share a tree read the same
-// nonzero (dim, val) -- a broadcast load -- and take their query's
+// nonzeros as (dim, value bits) pairs, two per 16-byte broadcast load, and take their query's
 // component from shared memory (odd row stride: no bank conflicts).  Each
 // projection is an fmaf chain in ascending dimension from +0.0f, followed by
 // the descent p <= split -> left (Algorithm 3).
@@ -41,8 +41,8 @@ constexpr int ROUTE_TREES_PER_ITEM = 16;
 template <int QB>
 __global__ void __launch_bounds__(512) k_query_route(
     const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
-    const int32_t *__restrict__ col_off, const int32_t *__restrict__ dim,
-    const float *__restrict__ val, const float *__restrict__ split, int32_t *__restrict__ leaf,
+    const int2 *__restrict__ rcol, const int2 *__restrict__ dv,
+    const float *__restrict__ split, int32_t *__restrict__ leaf,
     float *__restrict__ proj, uint32_t *__restrict__ status, int64_t n_items,
     const QueryRecord *__restrict__ rec) {
     extern __shared__ float qs[];  // QB x (d | 1)
@@ -116,21 +116,28 @@ __global__ void __launch_bounds__(512) k_query_route(
             int64_t node = 0;
             for (int j = 0; j < l; ++j) {
                 const int c = tt * l + j;
-                const int e1 = __ldg(col_off + c + 1);
-                int e = __ldg(col_off + c);
+                const int2 sc = __ldg(rcol + c);
+                const int4 *p4 = reinterpret_cast<const int4 *>(dv + sc.x);
                 float acc = 0.0f;
-                for (; e + 4 <= e1; e += 4) {
-                    const int d0 = __ldg(dim + e), d1 = __ldg(dim + e + 1);
-                    const int d2 = __ldg(dim + e + 2), d3 = __ldg(dim + e + 3);
-                    const float v0 = __ldg(val + e), v1 = __ldg(val + e + 1);
-                    const float v2 = __ldg(val + e + 2), v3 = __ldg(val + e + 3);
-                    const float x0 = qrow[d0], x1 = qrow[d1], x2 = qrow[d2], x3 = qrow[d3];
-                    acc = __fmaf_rn(x0, v0, acc);
-                    acc = __fmaf_rn(x1, v1, acc);
-                    acc = __fmaf_rn(x2, v2, acc);
-                    acc = __fmaf_rn(x3, v3, acc);
+                int k = 0;
+                for (; k + 4 <= sc.y; k += 4) {
+                    const int4 A = __ldg(p4 + (k >> 1)), B = __ldg(p4 + (k >> 1) + 1);
+                    const float x0 = qrow[A.x], x1 = qrow[A.z], x2 = qrow[B.x], x3 = qrow[B.z];
+                    acc = __fmaf_rn(x0, __int_as_float(A.y), acc);
+                    acc = __fmaf_rn(x1, __int_as_float(A.w), acc);
+                    acc = __fmaf_rn(x2, __int_as_float(B.y), acc);
+                    acc = __fmaf_rn(x3, __int_as_float(B.w), acc);
                 }
-                for (; e < e1; ++e) acc = __fmaf_rn(qrow[__ldg(dim + e)], __ldg(val + e), acc);
+                if (k + 2 <= sc.y) {
+                    const int4 A = __ldg(p4 + (k >> 1));
+                    acc = __fmaf_rn(qrow[A.x], __int_as_float(A.y), acc);
+                    acc = __fmaf_rn(qrow[A.z], __int_as_float(A.w), acc);
+                    k += 2;
+                }
+                if (k < sc.y) {
+                    const int2 P = __ldg(dv + sc.x + k);
+                    acc = __fmaf_rn(qrow[P.x], __int_as_float(P.y), acc);
+                }
                 if (proj != nullptr && live && tree_ok) proj[(q0 + qq) * ncols + c] = acc;
                 node = 2 * node + 1 + (acc > __ldg(sp + node) ? 1 : 0);
             }
@@ -264,6 +271,91 @@ __device__ __forceinline__ void rows_sq_dist(const float4 *const (&rows)[2],
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory atomic add at a 32-bit shared address; returns the old word.
+__device__ __forceinline__ uint32_t atom_add_shared_u32(uint32_t addr, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
+    return old;
+}
+
+// One lane's share of a vote window: four leaf entries e.x..e.w at
+// positions rel..rel+3 of a segment of length len.  Each entry in the
+// segment adds one vote to its 8-bit counter (the byte (id - c0) & 3 of word
+// (id - c0) >> 2 at shared address cnt_s); an entry outside the segment goes
+// to the lane's spare word instead.  Returns a bit per entry whose count went
+// from v-1 to v.  Written as one PTX block so that each step is one integer
+// instruction and all four atomics are in flight together.
+__device__ __forceinline__ uint32_t vote4(uint32_t cnt_s, int4 e, int32_t rel, int32_t len,
+                                          int32_t c0, uint32_t spare, uint32_t vm1) {
+    uint32_t emask;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p<4>, h<4>;\n\t"
+        ".reg .b32 t<4>, o<4>, s<4>, n<4>, r<4>, z, one;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "mov.b32 one, 1;\n\t"
+        "setp.lt.u32 p0, %6, %7;\n\t"
+        "add.u32 t1, %6, 1;\n\t"
+        "setp.lt.u32 p1, t1, %7;\n\t"
+        "add.u32 t2, %6, 2;\n\t"
+        "setp.lt.u32 p2, t2, %7;\n\t"
+        "add.u32 t3, %6, 3;\n\t"
+        "setp.lt.u32 p3, t3, %7;\n\t"
+        "sub.u32 o0, %2, %8;\n\t"
+        "sub.u32 o1, %3, %8;\n\t"
+        "sub.u32 o2, %4, %8;\n\t"
+        "sub.u32 o3, %5, %8;\n\t"
+        "selp.b32 o0, o0, %9, p0;\n\t"
+        "selp.b32 o1, o1, %9, p1;\n\t"
+        "selp.b32 o2, o2, %9, p2;\n\t"
+        "selp.b32 o3, o3, %9, p3;\n\t"
+        "shl.b32 s0, o0, 3;\n\t"
+        "shl.b32 s1, o1, 3;\n\t"
+        "shl.b32 s2, o2, 3;\n\t"
+        "shl.b32 s3, o3, 3;\n\t"
+        "shf.l.wrap.b32 n0, z, one, s0;\n\t"
+        "shf.l.wrap.b32 n1, z, one, s1;\n\t"
+        "shf.l.wrap.b32 n2, z, one, s2;\n\t"
+        "shf.l.wrap.b32 n3, z, one, s3;\n\t"
+        "and.b32 t0, o0, 0xfffffffc;\n\t"
+        "and.b32 t1, o1, 0xfffffffc;\n\t"
+        "and.b32 t2, o2, 0xfffffffc;\n\t"
+        "and.b32 t3, o3, 0xfffffffc;\n\t"
+        "add.u32 t0, t0, %1;\n\t"
+        "add.u32 t1, t1, %1;\n\t"
+        "add.u32 t2, t2, %1;\n\t"
+        "add.u32 t3, t3, %1;\n\t"
+        "atom.shared.add.u32 r0, [t0], n0;\n\t"
+        "atom.shared.add.u32 r1, [t1], n1;\n\t"
+        "atom.shared.add.u32 r2, [t2], n2;\n\t"
+        "atom.shared.add.u32 r3, [t3], n3;\n\t"
+        "shf.r.wrap.b32 r0, r0, z, s0;\n\t"
+        "shf.r.wrap.b32 r1, r1, z, s1;\n\t"
+        "shf.r.wrap.b32 r2, r2, z, s2;\n\t"
+        "shf.r.wrap.b32 r3, r3, z, s3;\n\t"
+        "and.b32 r0, r0, 255;\n\t"
+        "and.b32 r1, r1, 255;\n\t"
+        "and.b32 r2, r2, 255;\n\t"
+        "and.b32 r3, r3, 255;\n\t"
+        "setp.eq.and.u32 h0, r0, %10, p0;\n\t"
+        "setp.eq.and.u32 h1, r1, %10, p1;\n\t"
+        "setp.eq.and.u32 h2, r2, %10, p2;\n\t"
+        "setp.eq.and.u32 h3, r3, %10, p3;\n\t"
+        "selp.b32 %0, 1, 0, h0;\n\t"
+        "selp.b32 t1, 2, 0, h1;\n\t"
+        "selp.b32 t2, 4, 0, h2;\n\t"
+        "selp.b32 t3, 8, 0, h3;\n\t"
+        "or.b32 %0, %0, t1;\n\t"
+        "or.b32 t2, t2, t3;\n\t"
+        "or.b32 %0, %0, t2;\n\t"
+        "}"
+        : "=r"(emask)
+        : "r"(cnt_s), "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(rel), "r"(len), "r"(c0), "r"(spare),
+          "r"(vm1)
+        : "memory");
+    return emask;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -785,9 +877,11 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
 // ------------------------------------------------- vote / emit + search ----
 //
 // The batched path splits the query in two kernels:
-//   k_vote_emit  votes (as in k_vote_search) and writes each query's
-//                candidate set S to a per-query list in global memory; it
-//                carries no distance state, so a block has 16 warps.
+//   k_vote_emit  votes over 128-entry windows of the query's leaves (one
+//                16-byte load per lane, windows balanced over the warps) and
+//                writes each query's candidate set S to a per-query list in
+//                global memory; it carries no distance state, so a block
+//                has 16 warps.
 //   k_cand_knn   one warp per query: exact distances of the listed
 //                candidates (128-bit row loads, two rows in flight) and the
 //                warp's sorted top-k, written straight to the output row.
@@ -796,6 +890,7 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
 
 constexpr int VE_THREADS = 512;
 constexpr int VE_WARPS = VE_THREADS / 32;
+constexpr int VE_WIN = 128;  // leaf entries per warp window (4 per lane, one 16-byte load)
 
 struct VoteEmitArgs {
     int64_t n;
@@ -823,22 +918,39 @@ struct VoteEmitArgs {
     const QueryRecord *rec;  // plan mode: m of the batch
 };
 
+// Per query (one block, queries taken from an atomic counter):
+//   1. the query's leaf in each tree gives one segment of that tree's leaf
+//      array (ids ascending);
+//   2. per id chunk: clear the 8-bit counters; cut every segment to the ids
+//      of the chunk; split the segments into windows of 128 entries that
+//      start on a 4-entry boundary, so a lane reads its 4 entries with one
+//      16-byte load; each warp takes a contiguous run of windows (balanced
+//      over the block, whatever the leaf sizes);
+//   3. every valid entry adds one vote with a shared-memory atomic; the lane
+//      whose increment takes a count from v-1 to v appends the id to the
+//      query's list (Algorithm 4: a point enters S when its vote count
+//      reaches v).  List order is not fixed; the set is.
 __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs a0) {
     VoteEmitArgs a = a0;
     if (a.rec != nullptr) a.m = a.rec->m;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words
-    int32_t *cur = reinterpret_cast<int32_t *>(cnt + a.cnt_words);
-    int32_t *lend = cur + a.T_use;
-    int32_t *cend = lend + a.T_use;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words + 32 spare words
+    // per tree in this chunk: int4 index of the aligned segment start, and
+    // (segment length, entries before the segment in its first int4)
+    int64_t *tg4 = reinterpret_cast<int64_t *>(cnt + a.cnt_words + 32);
+    int2 *tlh = reinterpret_cast<int2 *>(tg4 + a.T_use);
+    int32_t *cur = reinterpret_cast<int32_t *>(tlh + a.T_use);     // first entry left, per tree
+    int32_t *lend = cur + a.T_use;                                  // end of the query's leaf
+    int32_t *cend = lend + a.T_use;                                 // end inside this chunk
+    int32_t *wpre = cend + a.T_use;                                 // T_use + 1: first window
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     const uint32_t vm1 = uint32_t(a.v - 1);
+    const int T = a.T_use;
 
     for (;;) {
         if (tid == 0) {
@@ -849,8 +961,8 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
         __syncthreads();
         const int64_t qi = s_q;
         if (qi < 0) break;
-        for (int t = tid; t < a.T_use; t += VE_THREADS) {
-            const int32_t lf = a.leaf_of_q[qi * a.T_use + t];
+        for (int t = tid; t < T; t += VE_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * T + t];
             cur[t] = a.leaf_off[lf];
             lend[t] = a.leaf_off[lf + 1];
         }
@@ -863,10 +975,12 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                 const int n4 = (nwords + 3) >> 2;
                 for (int w = tid; w < n4; w += VE_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
             }
-            __syncthreads();  // cur/lend written, counters cleared
+            // this chunk's part of every segment and its window count (the
+            // thread of tree t also wrote cur[t] and lend[t])
             const int64_t lim = c0 + CH_IDS;
-            for (int t = tid; t < a.T_use; t += VE_THREADS) {
+            for (int t = tid; t < T; t += VE_THREADS) {
                 int32_t lo = cur[t], hi = lend[t];
+                const int32_t p = lo;
                 if (lim < a.n) {
                     const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
                     while (lo < hi) {
@@ -876,92 +990,114 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                         else
                             hi = mid;
                     }
-                    cend[t] = lo;
-                } else {
-                    cend[t] = hi;
+                    hi = lo;
                 }
+                cend[t] = hi;
+                const int64_t g = int64_t(t) * a.n + p;
+                const int32_t head = int32_t(g & 3);
+                tg4[t] = (g - head) >> 2;
+                tlh[t] = make_int2(hi - p, head);
+                wpre[t] = p < hi ? (hi - p + head + VE_WIN - 1) / VE_WIN : 0;
             }
             __syncthreads();
-            // the warp's 128-id tiles, the next one loaded while the current
-            // one votes; all index arithmetic is 32-bit (ids < 2^31)
-            const int32_t c0i = int32_t(c0);
-            int t = warp;
-            int32_t p = 0, e = 0;
-            while (t < a.T_use) {
-                p = cur[t];
-                e = cend[t];
-                if (p < e) break;
-                t += VE_WARPS;
-            }
-            const int32_t *base = a.leaf_ids + int64_t(t < a.T_use ? t : 0) * a.n;
-            int32_t id[4];
-            {
-                const int rem = t < a.T_use ? e - p : 0;
+            if (warp == 0) {  // exclusive scan of the window counts
+                int run = 0;
+                for (int b = 0; b < T; b += 32) {
+                    const int t = b + lane;
+                    const int x = t < T ? wpre[t] : 0;
+                    int s = x;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    id[u] = (32 * u + lane < rem) ? __ldg(base + p + 32 * u + lane) : -1;
-            }
-            while (t < a.T_use) {
-                int tn = t;
-                int32_t pn = p + 128, en = e;
-                const int32_t *bn = base;
-                if (pn >= en) {
-                    if (lane == 0) cur[t] = en;
-                    tn = t + VE_WARPS;
-                    while (tn < a.T_use) {
-                        pn = cur[tn];
-                        en = cend[tn];
-                        if (pn < en) break;
-                        tn += VE_WARPS;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, s, o);
+                        if (lane >= o) s += y;
                     }
-                    bn = a.leaf_ids + int64_t(tn < a.T_use ? tn : 0) * a.n;
+                    if (t < T) wpre[t] = run + s - x;
+                    run += __shfl_sync(0xffffffffu, s, 31);
                 }
-                int32_t idn[4];
-                {
-                    const int rem = tn < a.T_use ? en - pn : 0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        idn[u] = (32 * u + lane < rem) ? __ldg(bn + pn + 32 * u + lane) : -1;
+                if (lane == 0) wpre[T] = run;
+            }
+            __syncthreads();
+            // this warp's windows [i0, i1)
+            const int W = wpre[T];
+            const int i0 = int((int64_t(W) * warp) / VE_WARPS);
+            const int i1 = int((int64_t(W) * (warp + 1)) / VE_WARPS);
+            int t = 0;
+            {
+                int hi = T;  // last tree whose first window is <= i0
+                while (hi - t > 1) {
+                    const int mid = (t + hi) >> 1;
+                    if (wpre[mid] <= i0)
+                        t = mid;
+                    else
+                        hi = mid;
                 }
-                // all four atomics first, then the emission test: the lane
-                // whose increment takes a count from v-1 to v emits the id
-                uint32_t old[4], sh[4];
+            }
+            const int32_t c0i = int32_t(c0);
+            // an entry outside the segment is redirected to the lane's spare
+            // counter word (past the chunk's words; never read back), so the
+            // vote loop has no branch per entry
+            const uint32_t spare = 4u * uint32_t(a.cnt_words + lane);
+            const uint32_t cnt_s = smem_u32(cnt);
+            if (i0 < i1) {
+                // fetch cursor: tree t, its windows [wf, wn), its segment
+                // (aligned start tp, head = entries before the segment start,
+                // length len)
+                int wf = wpre[t], wn = wpre[t + 1];
+                int32_t lrel = 0, len = 0;  // lane's first entry in the tree's first window
+                const int4 *tpl = nullptr;  // the lane's int4 in the tree's first window
+                auto load_tree = [&]() {
+                    const int2 lh = tlh[t];
+                    len = lh.x;
+                    lrel = 4 * lane - lh.y;
+                    tpl = reinterpret_cast<const int4 *>(a.leaf_ids) + tg4[t] + lane;
+                };
+                load_tree();
+                // window i: the lane's 4 entries q and the first one's
+                // position rel in the segment
+                auto fetch = [&](int i, int32_t &rel, int32_t &ln, int4 &q) {
+                    if (i >= wn) {
+                        do {
+                            ++t;
+                            wf = wn;
+                            wn = wpre[t + 1];
+                        } while (i >= wn);
+                        load_tree();
+                    }
+                    const int32_t j0 = (i - wf) * (VE_WIN / 4);
+                    rel = 4 * j0 + lrel;
+                    ln = len;
+                    if (rel < len) q = __ldg(tpl + j0);
+                };
+                auto vote = [&](const int4 &q, int32_t rel, int32_t ln) {
+                    const uint32_t emask = vote4(cnt_s, q, rel, ln, c0i, spare, vm1);
+                    if (emask != 0u) {
+                        const int32_t e[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t off = uint32_t(id[u] - c0i);
-                    sh[u] = (off & 3u) << 3;
-                    old[u] = id[u] >= 0 ? atomicAdd(&cnt[off >> 2], 1u << sh[u]) : 0u;
-                }
-                uint32_t emask = 0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    emask |= (id[u] >= 0 && ((old[u] >> sh[u]) & 0xffu) == vm1) ? (1u << u) : 0u;
-                if (__any_sync(0xffffffffu, emask != 0)) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const bool emit = (emask >> u) & 1u;
-                        const unsigned em = __ballot_sync(0xffffffffu, emit);
-                        if (em) {
-                            int b0 = 0;
-                            if (lane == 0) b0 = atomicAdd(&s_cnt, __popc(em));
-                            b0 = __shfl_sync(0xffffffffu, b0, 0);
-                            if (emit) {
-                                const int slot = b0 + __popc(em & lt);
-                                if (slot < a.capq) clist[slot] = id[u];
+                        for (int u = 0; u < 4; ++u) {
+                            if ((emask >> u) & 1u) {
+                                const int slot = atomicAdd(&s_cnt, 1);
+                                if (slot < a.capq) clist[slot] = e[u];
                                 if (a.dbg_cand != nullptr && slot < a.cand_cap)
-                                    a.dbg_cand[qi * a.cand_cap + slot] = id[u];
+                                    a.dbg_cand[qi * a.cand_cap + slot] = e[u];
                             }
                         }
                     }
+                };
+                // two windows per step, each loaded one window ahead
+                int32_t ra = 0, la = 0, rb = 0, lb = 0;
+                int4 qa = make_int4(0, 0, 0, 0), qb = make_int4(0, 0, 0, 0);
+                fetch(i0, ra, la, qa);
+                int i = i0;
+                for (; i + 1 < i1; i += 2) {
+                    fetch(i + 1, rb, lb, qb);
+                    vote(qa, ra, la);
+                    if (i + 2 < i1) fetch(i + 2, ra, la, qa);
+                    vote(qb, rb, lb);
                 }
-                t = tn;
-                p = pn;
-                e = en;
-                base = bn;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) id[u] = idn[u];
+                if (i < i1) vote(qa, ra, la);
             }
             __syncthreads();
+            for (int t2 = tid; t2 < T; t2 += VE_THREADS) cur[t2] = cend[t2];
             if (a.dbg_votes != nullptr) {
                 for (int w = tid; w < nwords; w += VE_THREADS) {
                     const uint32_t word = cnt[w];
@@ -970,8 +1106,8 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                         if (id2 < a.n) a.dbg_votes[qi * a.n + id2] = uint8_t((word >> (8 * b)) & 0xffu);
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
         if (tid == 0) {
             const int c = s_cnt;
@@ -1379,7 +1515,7 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
     const int64_t items = tiles * groups;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(sms) * std::max(per_sm, 1)));
     k_query_route<QB><<<unsigned(blocks), 512, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l,
-                                                         idx->L, idx->col_off, idx->dim, idx->val,
+                                                         idx->L, idx->rcol, idx->dv,
                                                          idx->split, ql.leaf, ql.proj, idx->status,
                                                          items, ql.rec);
     return cudaGetLastError();
@@ -1479,7 +1615,7 @@ cudaError_t launch_route_any(const mrpt_index *idx, const QueryLaunch &ql, cudaS
 cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
     const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
     const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
-    const size_t smem = size_t(cnt_words) * 4 + size_t(3 * ql.n_trees) * 4;
+    const size_t smem = size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 + size_t(4 * ql.n_trees + 1) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_vote_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
