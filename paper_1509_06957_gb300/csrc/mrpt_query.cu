@@ -227,6 +227,13 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// acc + (q - x)^2 per component, as packed two-lane float32 instructions
+// (each lane rounds exactly as the scalar __fadd_rn / __fmaf_rn would).
+__device__ __forceinline__ float2 sq_acc2(float2 q, float2 x, float2 acc) {
+    const float2 t = __fadd2_rn(q, make_float2(-x.x, -x.y));
+    return __ffma2_rn(t, t, acc);
+}
+
 // Squared Euclidean distances between the staged query and R rows (R <= 2):
 // every lane keeps up to 4 float4 loads per row in flight before it
 // accumulates, then the warp reduces each row's partial sums.
@@ -411,17 +418,14 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 // memory (consecutive float4 per lane: no bank conflicts).
 __device__ __forceinline__ float smem_row_sq_dist(const float4 *row, const float4 *q4, int nv4,
                                                   int lane) {
-    float a0 = 0.f, a1 = 0.f;
+    float2 a = make_float2(0.f, 0.f);  // (x and z terms, y and w terms)
     for (int j = lane; j < nv4; j += 32) {
         const float4 x = row[j];
         const float4 q = q4[j];
-        const float dx = q.x - x.x, dy = q.y - x.y, dz = q.z - x.z, dw = q.w - x.w;
-        a0 = __fmaf_rn(dx, dx, a0);
-        a1 = __fmaf_rn(dy, dy, a1);
-        a0 = __fmaf_rn(dz, dz, a0);
-        a1 = __fmaf_rn(dw, dw, a1);
+        a = sq_acc2(make_float2(q.x, q.y), make_float2(x.x, x.y), a);
+        a = sq_acc2(make_float2(q.z, q.w), make_float2(x.z, x.w), a);
     }
-    return warp_sum(a0 + a1);
+    return warp_sum(a.x + a.y);
 }
 
 // The same for a bfloat16 row: 8 components per 16-byte load, widened to
@@ -469,23 +473,20 @@ __device__ __forceinline__ float4 row_chunk<uint2>(const uint2 &x) {
 template <typename ROW>
 __device__ __forceinline__ void smem_rows2_sq_dist(const ROW *r0, const ROW *r1, const float4 *q4,
                                                    int nv4, int lane, float &d0, float &d1) {
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    // per row: (x and z terms, y and w terms)
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int j = lane; j < nv4; j += 32) {
         const float4 q = q4[j];
         const float4 x = row_chunk<ROW>(r0[j]);
         const float4 y = row_chunk<ROW>(r1[j]);
-        float t;
-        t = q.x - x.x; a0 = __fmaf_rn(t, t, a0);
-        t = q.y - x.y; a1 = __fmaf_rn(t, t, a1);
-        t = q.z - x.z; a0 = __fmaf_rn(t, t, a0);
-        t = q.w - x.w; a1 = __fmaf_rn(t, t, a1);
-        t = q.x - y.x; b0 = __fmaf_rn(t, t, b0);
-        t = q.y - y.y; b1 = __fmaf_rn(t, t, b1);
-        t = q.z - y.z; b0 = __fmaf_rn(t, t, b0);
-        t = q.w - y.w; b1 = __fmaf_rn(t, t, b1);
+        const float2 qlo = make_float2(q.x, q.y), qhi = make_float2(q.z, q.w);
+        a = sq_acc2(qlo, make_float2(x.x, x.y), a);
+        b = sq_acc2(qlo, make_float2(y.x, y.y), b);
+        a = sq_acc2(qhi, make_float2(x.z, x.w), a);
+        b = sq_acc2(qhi, make_float2(y.z, y.w), b);
     }
-    float sa = a0 + a1, sb = b0 + b1;
+    float sa = a.x + a.y, sb = b.x + b.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
@@ -509,23 +510,25 @@ __device__ __forceinline__ float4 e4m3x4_to_float4(uint32_t w) {
 __device__ __forceinline__ void smem_rows2_sq_dist_fp8(const uint32_t *r0, const uint32_t *r1,
                                                        float s0, float s1, const float4 *q4, int nv4,
                                                        int lane, float &d0, float &d1) {
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    const float2 ns0 = make_float2(-s0, -s0), ns1 = make_float2(-s1, -s1);
 #pragma unroll 2
     for (int j = lane; j < nv4; j += 32) {
         const float4 q = q4[j];
         const float4 x = e4m3x4_to_float4(r0[j]);
         const float4 y = e4m3x4_to_float4(r1[j]);
-        float t;
-        t = __fmaf_rn(-s0, x.x, q.x); a0 = __fmaf_rn(t, t, a0);
-        t = __fmaf_rn(-s0, x.y, q.y); a1 = __fmaf_rn(t, t, a1);
-        t = __fmaf_rn(-s0, x.z, q.z); a0 = __fmaf_rn(t, t, a0);
-        t = __fmaf_rn(-s0, x.w, q.w); a1 = __fmaf_rn(t, t, a1);
-        t = __fmaf_rn(-s1, y.x, q.x); b0 = __fmaf_rn(t, t, b0);
-        t = __fmaf_rn(-s1, y.y, q.y); b1 = __fmaf_rn(t, t, b1);
-        t = __fmaf_rn(-s1, y.z, q.z); b0 = __fmaf_rn(t, t, b0);
-        t = __fmaf_rn(-s1, y.w, q.w); b1 = __fmaf_rn(t, t, b1);
+        const float2 qlo = make_float2(q.x, q.y), qhi = make_float2(q.z, q.w);
+        float2 t;
+        t = __ffma2_rn(ns0, make_float2(x.x, x.y), qlo);
+        a = __ffma2_rn(t, t, a);
+        t = __ffma2_rn(ns1, make_float2(y.x, y.y), qlo);
+        b = __ffma2_rn(t, t, b);
+        t = __ffma2_rn(ns0, make_float2(x.z, x.w), qhi);
+        a = __ffma2_rn(t, t, a);
+        t = __ffma2_rn(ns1, make_float2(y.z, y.w), qhi);
+        b = __ffma2_rn(t, t, b);
     }
-    float sa = a0 + a1, sb = b0 + b1;
+    float sa = a.x + a.y, sb = b.x + b.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
