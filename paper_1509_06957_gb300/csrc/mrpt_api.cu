@@ -128,6 +128,8 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->split);
     cudaFree(idx->leaf_off);
     cudaFree(idx->leaf_ids);
+    cudaFree(idx->leaf4);
+    cudaFree(idx->leaf_off4);
     cudaFree(idx->Xb);
     cudaFree(idx->X8);
     cudaFree(idx->status);
@@ -311,6 +313,7 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
         if (e != cudaSuccess) return fail(cuda_fail(e, "mrpt_build: status"));
     }
     if ((rc = grow_trees_device(idx))) return fail(rc);
+    if ((rc = build_vote_layout(idx))) return fail(rc);
     *out = idx;
     return MRPT_OK;
 }
@@ -853,7 +856,7 @@ int mrpt_load(const char *path, mrpt_index **out) {
     }
     if (short_read) return fail(MRPT_ERR_INVALID_ARG, "mrpt_load: truncated file or leaf id out of range");
     fclose(f);
-    if ((rc = compute_leaf_offsets(idx)) || (rc = upload_route_pairs(idx))) {
+    if ((rc = compute_leaf_offsets(idx)) || (rc = upload_route_pairs(idx)) || (rc = build_vote_layout(idx))) {
         free_index(idx);
         return rc;
     }

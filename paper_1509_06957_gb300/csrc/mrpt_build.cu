@@ -478,6 +478,72 @@ int grow_trees_device(mrpt_index *idx) {
     return MRPT_OK;
 }
 
+namespace {
+
+// One thread per entry of the vote layout: entry r of tree t lies in the
+// leaf j with 4*off4[j] <= r < 4*off4[j+1] (binary search); it takes the
+// leaf's id at that position, or the sentinel past the leaf's end.
+__global__ void k_pad_leaves(const int32_t *__restrict__ leaf_ids, int64_t n, int32_t T,
+                             const int32_t *__restrict__ leaf_off, const int32_t *__restrict__ off4,
+                             int64_t L, int64_t s4, int32_t sentinel, int32_t *__restrict__ out) {
+    const int64_t per_tree = 4 * s4;
+    const int64_t total = int64_t(T) * per_tree;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = e / per_tree;
+        const int64_t r = e - t * per_tree;
+        int64_t lo = 0, hi = L;  // last leaf j with 4*off4[j] <= r
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (4 * int64_t(off4[mid]) <= r)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int64_t pos = r - 4 * int64_t(off4[lo]);
+        const int64_t size = int64_t(leaf_off[lo + 1]) - leaf_off[lo];
+        out[e] = pos < size ? leaf_ids[t * n + leaf_off[lo] + pos] : sentinel;
+    }
+}
+
+}  // namespace
+
+int build_vote_layout(mrpt_index *idx) {
+    if (idx->n > VOTE_CHUNK_IDS) return MRPT_OK;
+    const int64_t L = idx->L;
+    std::vector<int32_t> off(size_t(L + 1)), off4(size_t(L + 1));
+    cudaError_t e = cudaMemcpy(off.data(), idx->leaf_off, size_t(L + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "vote layout: leaf offsets");
+    int32_t longest = 0;
+    off4[0] = 0;
+    for (int64_t j = 0; j < L; ++j) {
+        const int32_t len4 = (off[size_t(j + 1)] - off[size_t(j)] + 3) / 4;
+        off4[size_t(j + 1)] = off4[size_t(j)] + len4;
+        longest = std::max(longest, len4);
+    }
+    const int64_t s4 = off4[size_t(L)];
+    const size_t bytes = size_t(idx->T) * size_t(s4 > 0 ? s4 : 1) * 16;
+    int rc;
+    if ((rc = dev_alloc((void **)&idx->leaf_off4, size_t(L + 1) * 4, "vote layout offsets"))) return rc;
+    if ((rc = dev_alloc((void **)&idx->leaf4, bytes, "vote layout"))) return rc;
+    idx->device_bytes += int64_t(bytes + size_t(L + 1) * 4);
+    idx->vote_s4 = s4;
+    idx->vote_win = (longest + 31) / 32;
+    e = cudaMemcpy(idx->leaf_off4, off4.data(), size_t(L + 1) * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "vote layout: offsets upload");
+    const int64_t total = int64_t(idx->T) * 4 * s4;
+    if (total > 0) {
+        const int blocks = int(std::min<int64_t>((total + 255) / 256, 152 * 32));
+        k_pad_leaves<<<blocks, 256, 0, idx->stream>>>(idx->leaf_ids, idx->n, idx->T, idx->leaf_off,
+                                                       idx->leaf_off4, L, s4, vote_sentinel(idx->n),
+                                                       reinterpret_cast<int32_t *>(idx->leaf4));
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "k_pad_leaves");
+    }
+    return MRPT_OK;
+}
+
 // Leaf offsets of a loaded index (they depend only on n and l).
 int compute_leaf_offsets(mrpt_index *idx) {
     const int blocks = int(std::min<int64_t>((idx->L + 1 + 255) / 256, 152 * 32));

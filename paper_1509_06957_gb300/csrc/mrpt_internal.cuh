@@ -73,6 +73,13 @@ struct mrpt_index {
     float *split = nullptr;      // T x (L-1)
     int32_t *leaf_off = nullptr; // L + 1 (identical for every tree)
     int32_t *leaf_ids = nullptr; // T x n
+    // Vote layout (only when n <= VOTE_CHUNK_IDS): leaf j of tree t starts at
+    // int4 index t*vote_s4 + leaf_off4[j] and holds the leaf's ids in
+    // ascending order, then the sentinel id up to a multiple of 4.
+    int4 *leaf4 = nullptr;
+    int32_t *leaf_off4 = nullptr; // L + 1
+    int64_t vote_s4 = 0;          // int4s per tree
+    int32_t vote_win = 0;         // 128-entry windows per leaf (the longest leaf)
     uint32_t *status = nullptr;  // [0] latched status bits, [1] work counter
 
     std::vector<int32_t> h_col_off, h_dim;
@@ -98,6 +105,24 @@ namespace mrpt {
 void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
                             std::vector<int32_t> &col_off, std::vector<int32_t> &dim,
                             std::vector<float> &val);
+
+// Ids whose 8-bit vote counters fit in shared memory at once (64 KB).
+constexpr int64_t VOTE_CHUNK_IDS = 65536;
+
+// 32-bit words of 8-bit vote counters for the ids of one chunk (a multiple
+// of 4 words); the word after them holds the sentinel's counter.
+inline int32_t vote_cnt_words(int64_t n) {
+    const int64_t ids = n < VOTE_CHUNK_IDS ? n : VOTE_CHUNK_IDS;
+    return int32_t(((ids + 3) / 4 + 3) & ~int64_t(3));
+}
+
+// Id that pads a leaf of the vote layout (its counter is the word after the
+// real ones; it is never reported as a candidate).
+inline int32_t vote_sentinel(int64_t n) { return 4 * vote_cnt_words(n); }
+
+// Builds idx->leaf4 / leaf_off4 from idx->leaf_ids (no-op when n is above
+// VOTE_CHUNK_IDS).
+int build_vote_layout(mrpt_index *idx);
 
 // Projections and median splits for every tree; fills idx->split,
 // idx->leaf_off and idx->leaf_ids.  X, R must already be on the device.

@@ -152,6 +152,7 @@ constexpr int VS_THREADS = 256;
 constexpr int VS_WARPS = VS_THREADS / 32;
 constexpr int CH_WORDS = 16384;          // 64 KB: 8-bit counters for 65,536 ids
 constexpr int64_t CH_IDS = int64_t(CH_WORDS) * 4;
+static_assert(CH_IDS == VOTE_CHUNK_IDS, "one id chunk per counter array");
 constexpr int32_t SENTINEL_ID = 0x7fffffff;
 
 __device__ __forceinline__ bool pair_less(float da, int32_t ia, float db, int32_t ib) {
@@ -361,6 +362,68 @@ __device__ __forceinline__ uint32_t vote4(uint32_t cnt_s, int4 e, int32_t rel, i
         : "=r"(emask)
         : "r"(cnt_s), "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(rel), "r"(len), "r"(c0), "r"(spare),
           "r"(vm1)
+        : "memory");
+    return emask;
+}
+
+// The same for four ids that need no range check (a lane either has four
+// entries of one padded leaf or none): ok == 0 turns the lane's four votes
+// off.  Counter byte id & 3 of word id >> 2 at cnt_s.
+__device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, uint32_t vm1) {
+    uint32_t emask;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h<4>;\n\t"
+        ".reg .b32 t<4>, s<4>, n<4>, r<4>, z, one;\n\t"
+        "setp.ne.u32 p, %5, 0;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "mov.b32 one, 1;\n\t"
+        "mov.b32 r0, 0;\n\t"
+        "mov.b32 r1, 0;\n\t"
+        "mov.b32 r2, 0;\n\t"
+        "mov.b32 r3, 0;\n\t"
+        "shl.b32 s0, %1, 3;\n\t"
+        "shl.b32 s1, %2, 3;\n\t"
+        "shl.b32 s2, %3, 3;\n\t"
+        "shl.b32 s3, %4, 3;\n\t"
+        "shf.l.wrap.b32 n0, z, one, s0;\n\t"
+        "shf.l.wrap.b32 n1, z, one, s1;\n\t"
+        "shf.l.wrap.b32 n2, z, one, s2;\n\t"
+        "shf.l.wrap.b32 n3, z, one, s3;\n\t"
+        "and.b32 t0, %1, 0xfffffffc;\n\t"
+        "and.b32 t1, %2, 0xfffffffc;\n\t"
+        "and.b32 t2, %3, 0xfffffffc;\n\t"
+        "and.b32 t3, %4, 0xfffffffc;\n\t"
+        "add.u32 t0, t0, %6;\n\t"
+        "add.u32 t1, t1, %6;\n\t"
+        "add.u32 t2, t2, %6;\n\t"
+        "add.u32 t3, t3, %6;\n\t"
+        "@p atom.shared.add.u32 r0, [t0], n0;\n\t"
+        "@p atom.shared.add.u32 r1, [t1], n1;\n\t"
+        "@p atom.shared.add.u32 r2, [t2], n2;\n\t"
+        "@p atom.shared.add.u32 r3, [t3], n3;\n\t"
+        "shf.r.wrap.b32 r0, r0, z, s0;\n\t"
+        "shf.r.wrap.b32 r1, r1, z, s1;\n\t"
+        "shf.r.wrap.b32 r2, r2, z, s2;\n\t"
+        "shf.r.wrap.b32 r3, r3, z, s3;\n\t"
+        "and.b32 r0, r0, 255;\n\t"
+        "and.b32 r1, r1, 255;\n\t"
+        "and.b32 r2, r2, 255;\n\t"
+        "and.b32 r3, r3, 255;\n\t"
+        "setp.eq.and.u32 h0, r0, %7, p;\n\t"
+        "setp.eq.and.u32 h1, r1, %7, p;\n\t"
+        "setp.eq.and.u32 h2, r2, %7, p;\n\t"
+        "setp.eq.and.u32 h3, r3, %7, p;\n\t"
+        "selp.b32 %0, 1, 0, h0;\n\t"
+        "selp.b32 t1, 2, 0, h1;\n\t"
+        "selp.b32 t2, 4, 0, h2;\n\t"
+        "selp.b32 t3, 8, 0, h3;\n\t"
+        "or.b32 %0, %0, t1;\n\t"
+        "or.b32 t2, t2, t3;\n\t"
+        "or.b32 %0, %0, t2;\n\t"
+        "}"
+        : "=r"(emask)
+        : "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(ok), "r"(cnt_s), "r"(vm1)
         : "memory");
     return emask;
 }
@@ -919,6 +982,12 @@ struct VoteEmitArgs {
     int32_t chunk;         // candidates per work item
     int32_t *done;         // per query: finished work items
     const QueryRecord *rec;  // plan mode: m of the batch
+    // vote layout (k_vote_flat)
+    const int4 *leaf4;
+    const int32_t *leaf_off4;
+    int64_t s4;
+    int32_t win;           // 128-entry windows per leaf
+    int32_t sentinel;
 };
 
 // Per query (one block, queries taken from an atomic counter):
@@ -1127,6 +1196,122 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
                 a.done[qi] = 0;
             }
         }
+    }
+}
+
+// k_vote_emit for an index whose ids fit one counter array (n <= 65,536),
+// over the vote layout: every leaf starts on a 16-byte boundary and is padded
+// with the sentinel to a multiple of 4 ids, so a lane's 16-byte load is four
+// ids of one leaf (or lies past the leaf and votes nothing), and every leaf
+// spans the same number of 128-entry windows (a.win).  Window i of the query
+// is window i % win of tree i / win; warps take contiguous runs of windows.
+__global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs a0) {
+    VoteEmitArgs a = a0;
+    if (a.rec != nullptr) a.m = a.rec->m;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words + 4 (sentinel word)
+    int64_t *sbase = reinterpret_cast<int64_t *>(cnt + a.cnt_words + 4);  // per tree: first int4
+    int32_t *slen = reinterpret_cast<int32_t *>(sbase + a.T_use);        // per tree: int4s
+    __shared__ int64_t s_q;
+    __shared__ int s_cnt;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const uint32_t vm1 = uint32_t(a.v - 1);
+    const int T = a.T_use;
+    const int K = a.win;
+    const int W = T * K;
+    const int i0 = int((int64_t(W) * warp) / VE_WARPS);
+    const int i1 = int((int64_t(W) * (warp + 1)) / VE_WARPS);
+    const uint32_t cnt_s = smem_u32(cnt);
+
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(a.work, 1u);
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+            s_cnt = 0;
+        }
+        {
+            uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+            const int n4 = a.cnt_words >> 2;
+            for (int w = tid; w < n4; w += VE_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi < 0) break;
+        for (int t = tid; t < T; t += VE_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * T + t];
+            const int32_t o = a.leaf_off4[lf];
+            sbase[t] = int64_t(t) * a.s4 + o;
+            slen[t] = a.leaf_off4[lf + 1] - o;
+        }
+        __syncthreads();
+        int32_t *clist = a.cand + qi * int64_t(a.capq);
+        auto emit = [&](const int4 &q, uint32_t emask) {
+            const int32_t e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (((emask >> u) & 1u) && e[u] != a.sentinel) {
+                    const int slot = atomicAdd(&s_cnt, 1);
+                    if (slot < a.capq) clist[slot] = e[u];
+                    if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = e[u];
+                }
+            }
+        };
+        // two windows per step, both loads in flight before either votes
+        int t = i0 / (K > 0 ? K : 1), k = i0 - t * K;
+        for (int i = i0; i < i1; i += 2) {
+            const int32_t ja = k * 32 + lane;
+            const uint32_t oka = ja < slen[t] ? 1u : 0u;
+            int4 qa = make_int4(0, 0, 0, 0), qb = make_int4(0, 0, 0, 0);
+            if (oka) qa = __ldg(a.leaf4 + sbase[t] + ja);
+            if (++k == K) {
+                k = 0;
+                ++t;
+            }
+            uint32_t okb = 0u;
+            if (i + 1 < i1) {
+                const int32_t jb = k * 32 + lane;
+                okb = jb < slen[t] ? 1u : 0u;
+                if (okb) qb = __ldg(a.leaf4 + sbase[t] + jb);
+                if (++k == K) {
+                    k = 0;
+                    ++t;
+                }
+            }
+            const uint32_t ea = vote4p(cnt_s, qa, oka, vm1);
+            const uint32_t eb = vote4p(cnt_s, qb, okb, vm1);
+            if ((ea | eb) != 0u) {
+                emit(qa, ea);
+                emit(qb, eb);
+            }
+        }
+        __syncthreads();
+        if (a.dbg_votes != nullptr) {
+            const int nwords = int((a.n + 3) >> 2);
+            for (int w = tid; w < nwords; w += VE_THREADS) {
+                const uint32_t word = cnt[w];
+                for (int b = 0; b < 4; ++b) {
+                    const int64_t id2 = 4 * int64_t(w) + b;
+                    if (id2 < a.n) a.dbg_votes[qi * a.n + id2] = uint8_t((word >> (8 * b)) & 0xffu);
+                }
+            }
+        }
+        if (tid == 0) {
+            const int c = s_cnt;
+            a.ncand[qi] = c;
+            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
+            if (c > a.capq) {
+                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
+            } else {
+                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
+                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
+                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
+                a.done[qi] = 0;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1616,14 +1801,16 @@ cudaError_t launch_route_any(const mrpt_index *idx, const QueryLaunch &ql, cudaS
 }
 
 cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
-    const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
-    const size_t smem = size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 + size_t(4 * ql.n_trees + 1) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_vote_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
+    const int cnt_words = vote_cnt_words(idx->n);
+    const bool flat = idx->leaf4 != nullptr;
+    auto kern = flat ? k_vote_flat : k_vote_emit;
+    const size_t smem = flat ? size_t(cnt_words + 4) * 4 + size_t(ql.n_trees) * 12
+                             : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
+                                   size_t(4 * ql.n_trees + 1) * 4;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_emit, VE_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VE_THREADS, smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
     if (e != cudaSuccess) return e;
@@ -1653,7 +1840,12 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.dbg_ncand = ql.n_cand;
     a.dbg_cand = ql.cand;
     a.cand_cap = ql.cand_cap;
-    k_vote_emit<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
+    a.leaf4 = idx->leaf4;
+    a.leaf_off4 = idx->leaf_off4;
+    a.s4 = idx->vote_s4;
+    a.win = idx->vote_win;
+    a.sentinel = vote_sentinel(idx->n);
+    kern<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
