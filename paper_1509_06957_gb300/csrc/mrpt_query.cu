@@ -366,10 +366,25 @@ __device__ __forceinline__ uint32_t vote4(uint32_t cnt_s, int4 e, int32_t rel, i
     return emask;
 }
 
+// 16-byte read-only load issued only when ok != 0 (no branch); when ok == 0
+// the result is unspecified and must not be used.
+__device__ __forceinline__ int4 ldg4_if(const int4 *p, uint32_t ok) {
+    int4 v;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %5, 0;\n\t"
+        "@q ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "r"(ok));
+    return v;
+}
+
 // The same for four ids that need no range check (a lane either has four
-// entries of one padded leaf or none): ok == 0 turns the lane's four votes
-// off.  Counter byte id & 3 of word id >> 2 at cnt_s.
-__device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, uint32_t vm1) {
+// entries of one padded leaf or none): ok == 0 sends the lane's four votes to
+// its own spare word at shared address spare (no branch; results ignored).
+// Counter byte id & 3 of word id >> 2 at cnt_s.
+__device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, uint32_t spare,
+                                           uint32_t vm1) {
     uint32_t emask;
     asm volatile(
         "{\n\t"
@@ -378,10 +393,6 @@ __device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, 
         "setp.ne.u32 p, %5, 0;\n\t"
         "mov.b32 z, 0;\n\t"
         "mov.b32 one, 1;\n\t"
-        "mov.b32 r0, 0;\n\t"
-        "mov.b32 r1, 0;\n\t"
-        "mov.b32 r2, 0;\n\t"
-        "mov.b32 r3, 0;\n\t"
         "shl.b32 s0, %1, 3;\n\t"
         "shl.b32 s1, %2, 3;\n\t"
         "shl.b32 s2, %3, 3;\n\t"
@@ -398,10 +409,14 @@ __device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, 
         "add.u32 t1, t1, %6;\n\t"
         "add.u32 t2, t2, %6;\n\t"
         "add.u32 t3, t3, %6;\n\t"
-        "@p atom.shared.add.u32 r0, [t0], n0;\n\t"
-        "@p atom.shared.add.u32 r1, [t1], n1;\n\t"
-        "@p atom.shared.add.u32 r2, [t2], n2;\n\t"
-        "@p atom.shared.add.u32 r3, [t3], n3;\n\t"
+        "selp.b32 t0, t0, %7, p;\n\t"
+        "selp.b32 t1, t1, %7, p;\n\t"
+        "selp.b32 t2, t2, %7, p;\n\t"
+        "selp.b32 t3, t3, %7, p;\n\t"
+        "atom.shared.add.u32 r0, [t0], n0;\n\t"
+        "atom.shared.add.u32 r1, [t1], n1;\n\t"
+        "atom.shared.add.u32 r2, [t2], n2;\n\t"
+        "atom.shared.add.u32 r3, [t3], n3;\n\t"
         "shf.r.wrap.b32 r0, r0, z, s0;\n\t"
         "shf.r.wrap.b32 r1, r1, z, s1;\n\t"
         "shf.r.wrap.b32 r2, r2, z, s2;\n\t"
@@ -410,10 +425,10 @@ __device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, 
         "and.b32 r1, r1, 255;\n\t"
         "and.b32 r2, r2, 255;\n\t"
         "and.b32 r3, r3, 255;\n\t"
-        "setp.eq.and.u32 h0, r0, %7, p;\n\t"
-        "setp.eq.and.u32 h1, r1, %7, p;\n\t"
-        "setp.eq.and.u32 h2, r2, %7, p;\n\t"
-        "setp.eq.and.u32 h3, r3, %7, p;\n\t"
+        "setp.eq.and.u32 h0, r0, %8, p;\n\t"
+        "setp.eq.and.u32 h1, r1, %8, p;\n\t"
+        "setp.eq.and.u32 h2, r2, %8, p;\n\t"
+        "setp.eq.and.u32 h3, r3, %8, p;\n\t"
         "selp.b32 %0, 1, 0, h0;\n\t"
         "selp.b32 t1, 2, 0, h1;\n\t"
         "selp.b32 t2, 4, 0, h2;\n\t"
@@ -423,7 +438,7 @@ __device__ __forceinline__ uint32_t vote4p(uint32_t cnt_s, int4 e, uint32_t ok, 
         "or.b32 %0, %0, t2;\n\t"
         "}"
         : "=r"(emask)
-        : "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(ok), "r"(cnt_s), "r"(vm1)
+        : "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(ok), "r"(cnt_s), "r"(spare), "r"(vm1)
         : "memory");
     return emask;
 }
@@ -1209,8 +1224,10 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
     VoteEmitArgs a = a0;
     if (a.rec != nullptr) a.m = a.rec->m;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words + 4 (sentinel word)
-    int64_t *sbase = reinterpret_cast<int64_t *>(cnt + a.cnt_words + 4);  // per tree: first int4
+    // cnt_words counter words, the sentinel's word (+3 unused), a spare word
+    // per lane
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);
+    int64_t *sbase = reinterpret_cast<int64_t *>(cnt + a.cnt_words + 36);  // per tree: first int4
     int32_t *slen = reinterpret_cast<int32_t *>(sbase + a.T_use);        // per tree: int4s
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
@@ -1225,6 +1242,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
     const int i0 = int((int64_t(W) * warp) / VE_WARPS);
     const int i1 = int((int64_t(W) * (warp + 1)) / VE_WARPS);
     const uint32_t cnt_s = smem_u32(cnt);
+    const uint32_t spare = cnt_s + 4u * uint32_t(a.cnt_words + 4 + lane);
 
     for (;;) {
         if (tid == 0) {
@@ -1259,29 +1277,23 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                 }
             }
         };
-        // two windows per step, both loads in flight before either votes
+        // two windows per step, both loads in flight before either votes;
+        // a window past i1 (odd count) votes nothing
         int t = i0 / (K > 0 ? K : 1), k = i0 - t * K;
         for (int i = i0; i < i1; i += 2) {
             const int32_t ja = k * 32 + lane;
             const uint32_t oka = ja < slen[t] ? 1u : 0u;
-            int4 qa = make_int4(0, 0, 0, 0), qb = make_int4(0, 0, 0, 0);
-            if (oka) qa = __ldg(a.leaf4 + sbase[t] + ja);
-            if (++k == K) {
-                k = 0;
-                ++t;
-            }
-            uint32_t okb = 0u;
-            if (i + 1 < i1) {
-                const int32_t jb = k * 32 + lane;
-                okb = jb < slen[t] ? 1u : 0u;
-                if (okb) qb = __ldg(a.leaf4 + sbase[t] + jb);
-                if (++k == K) {
-                    k = 0;
-                    ++t;
-                }
-            }
-            const uint32_t ea = vote4p(cnt_s, qa, oka, vm1);
-            const uint32_t eb = vote4p(cnt_s, qb, okb, vm1);
+            const int4 qa = ldg4_if(a.leaf4 + sbase[t] + ja, oka);
+            k = k + 1 == K ? 0 : k + 1;
+            t = k == 0 ? t + 1 : t;
+            const int tb = t < T ? t : T - 1;
+            const int32_t jb = k * 32 + lane;
+            const uint32_t okb = (i + 1 < i1 && jb < slen[tb]) ? 1u : 0u;
+            const int4 qb = ldg4_if(a.leaf4 + sbase[tb] + jb, okb);
+            k = k + 1 == K ? 0 : k + 1;
+            t = k == 0 ? t + 1 : t;
+            const uint32_t ea = vote4p(cnt_s, qa, oka, spare, vm1);
+            const uint32_t eb = vote4p(cnt_s, qb, okb, spare, vm1);
             if ((ea | eb) != 0u) {
                 emit(qa, ea);
                 emit(qb, eb);
@@ -1804,7 +1816,7 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     const int cnt_words = vote_cnt_words(idx->n);
     const bool flat = idx->leaf4 != nullptr;
     auto kern = flat ? k_vote_flat : k_vote_emit;
-    const size_t smem = flat ? size_t(cnt_words + 4) * 4 + size_t(ql.n_trees) * 12
+    const size_t smem = flat ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 12
                              : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
                                    size_t(4 * ql.n_trees + 1) * 4;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
