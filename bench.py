@@ -335,7 +335,10 @@ def run_gpu(args):
                 "peak_kind": f"{peak_kind} hbm_gbs", "kernel": name,
                 "algorithmic_bytes_per_query": round(per_query, 1), "avg_ms": round(ms, 4)}
 
-    r_vote = roof("k_vote_search" if args.path == 1 else "k_vote_emit", vote_bytes, vote_avg)
+    # ids of at most 65,536 points fit one counter array: the vote kernel
+    # then reads the padded leaf layout (k_vote_flat)
+    vote_kernel = "k_vote_search" if args.path == 1 else ("k_vote_flat" if n <= 65536 else "k_vote_emit")
+    r_vote = roof(vote_kernel, vote_bytes, vote_avg)
     rooflines = [r_vote]
     if args.path == 0:
         r_search = roof("k_cand_knn", search_bytes, search_avg)
