@@ -1002,6 +1002,7 @@ struct VoteEmitArgs {
     const int32_t *leaf_off4;
     int64_t s4;
     int32_t win;           // 128-entry windows per leaf
+    uint64_t win_magic;    // ceil(2^32 / win): i / win = (i * win_magic) >> 32 for i < 256 * win
     int32_t sentinel;
 };
 
@@ -1231,40 +1232,52 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
     int32_t *slen = reinterpret_cast<int32_t *>(sbase + a.T_use);        // per tree: int4s
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
+    __shared__ int s_win;  // next window of the query
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int warp = tid >> 5;
     const uint32_t vm1 = uint32_t(a.v - 1);
     const int T = a.T_use;
     const int K = a.win;
     const int W = T * K;
-    const int i0 = int((int64_t(W) * warp) / VE_WARPS);
-    const int i1 = int((int64_t(W) * (warp + 1)) / VE_WARPS);
     const uint32_t cnt_s = smem_u32(cnt);
     const uint32_t spare = cnt_s + 4u * uint32_t(a.cnt_words + 4 + lane);
 
-    for (;;) {
-        if (tid == 0) {
-            const uint32_t w = atomicAdd(a.work, 1u);
-            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
-            s_cnt = 0;
+    // The next query is claimed, and its leaves looked up, while the current
+    // one votes: thread t < T (T <= 255 < VE_THREADS) keeps tree t's leaf of
+    // the next query in registers.
+    if (tid == 0) {
+        const uint32_t w = atomicAdd(a.work, 1u);
+        s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+    }
+    __syncthreads();
+    int64_t qi = s_q;
+    int32_t pf_o = 0, pf_e = 0;
+    if (qi >= 0 && tid < T) {
+        const int32_t lf = a.leaf_of_q[qi * T + tid];
+        pf_o = a.leaf_off4[lf];
+        pf_e = a.leaf_off4[lf + 1];
+    }
+    while (qi >= 0) {
+        if (tid < T) {
+            sbase[tid] = int64_t(tid) * a.s4 + pf_o;
+            slen[tid] = pf_e - pf_o;
         }
         {
             uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
             const int n4 = a.cnt_words >> 2;
             for (int w = tid; w < n4; w += VE_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        const int64_t qi = s_q;
-        if (qi < 0) break;
-        for (int t = tid; t < T; t += VE_THREADS) {
-            const int32_t lf = a.leaf_of_q[qi * T + t];
-            const int32_t o = a.leaf_off4[lf];
-            sbase[t] = int64_t(t) * a.s4 + o;
-            slen[t] = a.leaf_off4[lf + 1] - o;
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(a.work, 1u);
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+            s_cnt = 0;
+            s_win = 0;
         }
         __syncthreads();
+        const int64_t qn = s_q;
+        int32_t pf_lf = 0;
+        if (qn >= 0 && tid < T) pf_lf = __ldg(a.leaf_of_q + qn * T + tid);
         int32_t *clist = a.cand + qi * int64_t(a.capq);
         auto emit = [&](const int4 &q, uint32_t emask) {
             const int32_t e[4] = {q.x, q.y, q.z, q.w};
@@ -1277,10 +1290,15 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                 }
             }
         };
-        // two windows per step, both loads in flight before either votes;
-        // a window past i1 (odd count) votes nothing
-        int t = i0 / (K > 0 ? K : 1), k = i0 - t * K;
-        for (int i = i0; i < i1; i += 2) {
+        // warps claim two windows at a time from a shared counter (so they
+        // finish together); both loads are in flight before either votes,
+        // and a window past W votes nothing
+        for (;;) {
+            int i = 0;
+            if (lane == 0) i = atomicAdd(&s_win, 2);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= W) break;
+            int t = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32), k = i - t * K;
             const int32_t ja = k * 32 + lane;
             const uint32_t oka = ja < slen[t] ? 1u : 0u;
             const int4 qa = ldg4_if(a.leaf4 + sbase[t] + ja, oka);
@@ -1288,10 +1306,8 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
             t = k == 0 ? t + 1 : t;
             const int tb = t < T ? t : T - 1;
             const int32_t jb = k * 32 + lane;
-            const uint32_t okb = (i + 1 < i1 && jb < slen[tb]) ? 1u : 0u;
+            const uint32_t okb = (i + 1 < W && jb < slen[tb]) ? 1u : 0u;
             const int4 qb = ldg4_if(a.leaf4 + sbase[tb] + jb, okb);
-            k = k + 1 == K ? 0 : k + 1;
-            t = k == 0 ? t + 1 : t;
             const uint32_t ea = vote4p(cnt_s, qa, oka, spare, vm1);
             const uint32_t eb = vote4p(cnt_s, qb, okb, spare, vm1);
             if ((ea | eb) != 0u) {
@@ -1299,7 +1315,11 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                 emit(qb, eb);
             }
         }
-        __syncthreads();
+        if (qn >= 0 && tid < T) {
+            pf_o = __ldg(a.leaf_off4 + pf_lf);
+            pf_e = __ldg(a.leaf_off4 + pf_lf + 1);
+        }
+        __syncthreads();  // every vote of this query is in
         if (a.dbg_votes != nullptr) {
             const int nwords = int((a.n + 3) >> 2);
             for (int w = tid; w < nwords; w += VE_THREADS) {
@@ -1309,6 +1329,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                     if (id2 < a.n) a.dbg_votes[qi * a.n + id2] = uint8_t((word >> (8 * b)) & 0xffu);
                 }
             }
+            __syncthreads();
         }
         if (tid == 0) {
             const int c = s_cnt;
@@ -1323,7 +1344,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                 a.done[qi] = 0;
             }
         }
-        __syncthreads();
+        qi = qn;
     }
 }
 
@@ -1856,6 +1877,7 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.leaf_off4 = idx->leaf_off4;
     a.s4 = idx->vote_s4;
     a.win = idx->vote_win;
+    a.win_magic = ((uint64_t(1) << 32) + uint64_t(idx->vote_win) - 1) / uint64_t(std::max(idx->vote_win, 1));
     a.sentinel = vote_sentinel(idx->n);
     kern<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
