@@ -71,6 +71,12 @@ def _load():
             lib.orc_random_matrix.restype = ctypes.c_int64
             lib.orc_random_matrix.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_float, ctypes.c_uint64, _i32p, _i32p, _f32p]
+            lib.orc_random_matrix_fixed.restype = ctypes.c_int64
+            lib.orc_random_matrix_fixed.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_float, ctypes.c_uint64, _i32p, _i32p,
+                                                    _f32p]
+            lib.orc_fixed_count.restype = ctypes.c_int32
+            lib.orc_fixed_count.argtypes = [ctypes.c_float, ctypes.c_int32]
             lib.orc_project.restype = None
             lib.orc_project.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                         _i32p, _i32p, _f32p, _f32p]
@@ -147,16 +153,27 @@ class RandomMatrix:
         return R
 
 
-def random_matrix(T: int, l: int, d: int, density: float, seed: int) -> RandomMatrix:
-    """Sparse random vectors of Algorithm 1 (Sec. II-B, II-C)."""
+SPARSITY_BERNOULLI = 0  # each component nonzero with probability a (Sec. II-B)
+SPARSITY_FIXED = 1      # exactly ceil(a d) nonzeros per vector (Sec. II-B footnote)
+
+
+def fixed_count(density: float, d: int) -> int:
+    """Nonzeros per vector of the fixed-count variant: ceil(a d) in [1, d]."""
+    return int(_load().orc_fixed_count(ctypes.c_float(density).value, d))
+
+
+def random_matrix(T: int, l: int, d: int, density: float, seed: int,
+                  sparsity: int = SPARSITY_BERNOULLI) -> RandomMatrix:
+    """Sparse random vectors of Algorithm 1 (Sec. II-B, II-C); with
+    sparsity=SPARSITY_FIXED, the footnote's variant of Sec. II-B."""
     lib = _load()
+    fn = lib.orc_random_matrix_fixed if sparsity == SPARSITY_FIXED else lib.orc_random_matrix
     col_off = np.zeros(T * l + 1, dtype=np.int32)
     dens = ctypes.c_float(density).value
-    nnz = lib.orc_random_matrix(T, l, d, dens, seed, _p(col_off, _i32p), None, None)
+    nnz = fn(T, l, d, dens, seed, _p(col_off, _i32p), None, None)
     dim = np.zeros(max(nnz, 1), dtype=np.int32)
     val = np.zeros(max(nnz, 1), dtype=np.float32)
-    lib.orc_random_matrix(T, l, d, dens, seed, _p(col_off, _i32p), _p(dim, _i32p),
-                          _p(val, _f32p))
+    fn(T, l, d, dens, seed, _p(col_off, _i32p), _p(dim, _i32p), _p(val, _f32p))
     return RandomMatrix(col_off, dim[:nnz].copy(), val[:nnz].copy(), d)
 
 
@@ -215,12 +232,12 @@ class Index:
 
 
 def grow_trees(X: np.ndarray, T: int, l: int, density: float, seed: int,
-               R: RandomMatrix | None = None) -> Index:
+               R: RandomMatrix | None = None, sparsity: int = SPARSITY_BERNOULLI) -> Index:
     """Algorithm 1: random matrix, projection, then one tree per t."""
     X = _f32(X)
     n, d = X.shape
     if R is None:
-        R = random_matrix(T, l, d, density, seed)
+        R = random_matrix(T, l, d, density, seed, sparsity)
     P = project(X, R)
     L = 1 << l
     split = np.zeros((T, max(L - 1, 0)), dtype=np.float32)

@@ -11,6 +11,8 @@
  *   - orc_random_matrix : Algorithm 1, inner two loops; Sec. II-B (sparse
  *                         vectors r_i ~ N(0,1) w.p. a, else 0); Sec. II-C (one
  *                         vector per tree level, R in R^{d x l}).
+ *   - orc_random_matrix_fixed : the footnote of Sec. II-B (exactly ceil(a d)
+ *                         nonzeros per vector), the ablation of Table III.
  *   - orc_project       : Algorithm 1 (P = XR) and Algorithm 3 (p = q^T R).
  *   - orc_grow_tree     : Algorithm 2 with the order-based median of Sec. II-A
  *                         (first ceil(c/2) points by projected order go left).
@@ -101,6 +103,81 @@ int64_t orc_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64
     return nnz;
 }
 
+/*
+ * Number of nonzeros per vector in the fixed-count variant: ceil(a d),
+ * clamped to [1, d].  a arrives as a float, so a*d is computed in double with
+ * a relative allowance of 1e-6 (1/sqrt(784) as a float times 784 is
+ * 28.0000013, meant as 28).
+ */
+int32_t orc_fixed_count(float density, int32_t d)
+{
+    double k = ceil((double)density * (double)d * (1.0 - 1e-6));
+    if (k < 1.0) k = 1.0;
+    if (k > (double)d) k = (double)d;
+    return (int32_t)k;
+}
+
+typedef struct { double z; int32_t i; } draw_dim;
+
+static int cmp_draw_dim(const void *pa, const void *pb)
+{
+    const draw_dim *a = (const draw_dim *)pa, *b = (const draw_dim *)pb;
+    if (a->z < b->z) return -1;
+    if (a->z > b->z) return 1;
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+static int cmp_i32(const void *pa, const void *pb)
+{
+    const int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    return (a > b) - (a < b);
+}
+
+/*
+ * The ablation in the footnote of Sec. II-B: every vector has exactly
+ * k = orc_fixed_count(density, d) nonzeros instead of a Bernoulli(a) draw per
+ * component.  Reading: column c's nonzero dimensions are the k dimensions
+ * with the smallest (z_i, i), where z_i is the same uniform draw (counter
+ * 3(c d + i)) that the Bernoulli variant compares with a -- a uniformly
+ * random k-subset -- and their values are the same Box-Muller normals
+ * (counters 3(c d + i) + 1, + 2).  Output as in orc_random_matrix (always
+ * T*l*k nonzeros; dim and val may be NULL).
+ */
+int64_t orc_random_matrix_fixed(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
+                                int32_t *col_off, int32_t *dim, float *val)
+{
+    const int32_t k = orc_fixed_count(density, d);
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    draw_dim *dd = (draw_dim *)malloc(sizeof(draw_dim) * (size_t)d);
+    int32_t *pick = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    int64_t nnz = 0;
+    for (int32_t c = 0; c < T * l; ++c) {
+        col_off[c] = (int32_t)nnz;
+        if (dim && val) {
+            for (int32_t i = 0; i < d; ++i) {
+                const uint64_t ctr = 3ULL * (((uint64_t)c * (uint64_t)d) + (uint64_t)i);
+                dd[i].z = unit_open_right(orc_splitmix64(seed, ctr));
+                dd[i].i = i;
+            }
+            qsort(dd, (size_t)d, sizeof(draw_dim), cmp_draw_dim);
+            for (int32_t r = 0; r < k; ++r) pick[r] = dd[r].i;
+            qsort(pick, (size_t)k, sizeof(int32_t), cmp_i32);
+            for (int32_t r = 0; r < k; ++r) {
+                const uint64_t ctr = 3ULL * (((uint64_t)c * (uint64_t)d) + (uint64_t)pick[r]);
+                const double u1 = unit_open_left(orc_splitmix64(seed, ctr + 1));
+                const double u2 = unit_open_right(orc_splitmix64(seed, ctr + 2));
+                dim[nnz + r] = pick[r];
+                val[nnz + r] = (float)(sqrt(-2.0 * log(u1)) * cos(two_pi * u2));
+            }
+        }
+        nnz += k;
+    }
+    col_off[T * l] = (int32_t)nnz;
+    free(dd);
+    free(pick);
+    return nnz;
+}
+
 /* --------------------------------------------------------- projection ---- */
 
 /* One projection: sum over the column's nonzeros in ascending dimension, each
@@ -133,12 +210,6 @@ static int cmp_keyed(const void *pa, const void *pb)
     if (a->key < b->key) return -1;
     if (a->key > b->key) return 1;
     return (a->id > b->id) - (a->id < b->id);
-}
-
-static int cmp_i32(const void *pa, const void *pb)
-{
-    const int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
-    return (a > b) - (a < b);
 }
 
 typedef struct {

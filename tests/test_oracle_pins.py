@@ -69,6 +69,69 @@ def test_random_matrix_prefix_stable_in_T():
     assert not np.array_equal(a.val, c.val[: len(a.val)]) or len(a.val) != len(c.val)
 
 
+def test_fixed_count_variant_counts():
+    """Footnote of Sec. II-B: exactly ceil(a d) nonzeros per vector (at
+    least 1, at most d); values worked by hand."""
+    for (a, d, k) in [(1.0 / math.sqrt(784), 784, 28), (0.3, 50, 15), (0.01, 50, 1),
+                      (1.0, 50, 50), (1.0 / math.sqrt(128), 128, 12), (0.125, 64, 8)]:
+        assert oracle.fixed_count(a, d) == k
+        R = oracle.random_matrix(5, 3, d, a, seed=2, sparsity=oracle.SPARSITY_FIXED)
+        assert np.all(np.diff(R.col_off) == k)
+        for c in range(R.ncols):
+            seg = R.dim[R.col_off[c]:R.col_off[c + 1]]
+            assert np.all(np.diff(seg) > 0) and seg.min() >= 0 and seg.max() < d
+
+
+def test_fixed_count_variant_nests_with_bernoulli_variant():
+    """Both variants take the dimensions with the smallest first draw (the
+    Bernoulli variant those below a, the fixed one the k smallest), so per
+    column one set contains the other and shared dimensions carry the same
+    normal value."""
+    d, seed = 200, 5
+    for a in (0.03, 0.1, 0.4):
+        F = oracle.random_matrix(6, 4, d, a, seed, sparsity=oracle.SPARSITY_FIXED)
+        B = oracle.random_matrix(6, 4, d, a, seed)
+        for c in range(F.ncols):
+            fd = F.dim[F.col_off[c]:F.col_off[c + 1]]
+            fv = F.val[F.col_off[c]:F.col_off[c + 1]]
+            bd = B.dim[B.col_off[c]:B.col_off[c + 1]]
+            bv = B.val[B.col_off[c]:B.col_off[c + 1]]
+            sf, sb = set(fd.tolist()), set(bd.tolist())
+            assert sf <= sb or sb <= sf
+            common = sorted(sf & sb)
+            assert np.array_equal(fv[np.searchsorted(fd, common)], bv[np.searchsorted(bd, common)])
+    # density 1: both are the dense matrix
+    F = oracle.random_matrix(2, 3, 40, 1.0, 9, sparsity=oracle.SPARSITY_FIXED)
+    B = oracle.random_matrix(2, 3, 40, 1.0, 9)
+    assert np.array_equal(F.col_off, B.col_off) and np.array_equal(F.dim, B.dim)
+    assert np.array_equal(F.val, B.val)
+
+
+def test_fixed_count_variant_statistics_and_nesting():
+    """A uniformly random k-subset per vector with N(0,1) values; a larger k
+    keeps the smaller k's dimensions; the first trees are prefix-stable."""
+    from scipy import stats
+    T, l, d = 40, 8, 784
+    a = 1.0 / math.sqrt(d)
+    R = oracle.random_matrix(T, l, d, a, 7, sparsity=oracle.SPARSITY_FIXED)
+    nnz = len(R.val)
+    assert nnz == T * l * 28
+    vals = R.val.astype(np.float64)
+    assert abs(vals.mean()) < 5 / math.sqrt(nnz)
+    assert abs(vals.var() - 1.0) < 5 * math.sqrt(2.0 / nnz)
+    assert stats.kstest(vals, "norm").pvalue > 1e-4
+    counts = np.bincount(R.dim, minlength=d)
+    chi2 = ((counts - nnz / d) ** 2 / (nnz / d)).sum()
+    assert stats.chi2.sf(chi2, d - 1) > 1e-4
+    big = oracle.random_matrix(T, l, d, 2 * a, 7, sparsity=oracle.SPARSITY_FIXED)
+    for c in range(0, R.ncols, 7):
+        small = set(R.dim[R.col_off[c]:R.col_off[c + 1]].tolist())
+        assert small <= set(big.dim[big.col_off[c]:big.col_off[c + 1]].tolist())
+    few = oracle.random_matrix(3, l, d, a, 7, sparsity=oracle.SPARSITY_FIXED)
+    assert np.array_equal(few.dim, R.dim[:len(few.dim)])
+    assert np.array_equal(few.val, R.val[:len(few.val)])
+
+
 # ---------------------------------------------------------- projection ----
 
 def _round_to_f32(x: Fraction) -> np.float32:
