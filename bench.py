@@ -624,6 +624,87 @@ def run_reference(args):
     return out
 
 
+# ----------------------------------------------------- Pareto / ablation --
+
+def _front(points):
+    """Non-dominated (recall up, queries/s up) points, by recall."""
+    front = []
+    for p in sorted(points, key=lambda p: (-p["qps"], -p["recall"])):
+        if not front or p["recall"] > front[-1]["recall"]:
+            front.append(p)
+    return sorted(front, key=lambda p: p["recall"])
+
+
+def run_pareto(args):
+    """--workload pareto: the paper's parameter search (Sec. IV-B: grid over
+    T, depth and v with a = 1/sqrt(d)) as Pareto fronts of queries/s against
+    recall@k for k in {1, 10, 100}, for MRPT and the ablations of Table III:
+    fixed-count sparse vectors (exactly ceil(a d) nonzeros, the Sec. II-B
+    footnote), sparse trees without voting (v = 1), and classic dense RP
+    trees (a = 1, v = 1).  Also MRPT on the "Random" set (unit-length
+    N(0, I), 50,000 x 4096, Sec. IV-A).  Time is the library's device time of
+    one query pass (L2 flushed before it); recall is tie-aware."""
+    import torch
+    import paper_1509_06957_gb300 as mr
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stage = np.zeros(4, np.float32)
+    T_grid = (10, 25, 50, 100, 200)
+
+    def sweep(X, Q, variants, depths, ks):
+        m = Q.shape[0]
+        kmax = max(ks)
+        gt_ids, _ = exact_knn_gpu(X, Q, kmax, torch)
+        gt_d = torch.cat([((X[gt_ids[s:s + 256].long()].double() - Q[s:s + 256].double()[:, None, :]) ** 2)
+                          .sum(2).sqrt() for s in range(0, m, 256)])
+        n = X.shape[0]
+        out = {}
+        for name, density, sparsity, v_grid in variants:
+            pts = {k: [] for k in ks}
+            for l in depths:
+                index = mr.mrpt_build(X, max(T_grid), l, density, seed=0, sparsity=sparsity)
+                leaf = -(-n // (1 << l))
+                for T_use in T_grid:
+                    for v in v_grid:
+                        # |S| <= T ceil(n / 2^l) / v; settings with more than
+                        # 40,000 candidates per query are left out (seconds per pass)
+                        if v > T_use or T_use * leaf / v > 40000:
+                            continue
+                        for k in ks:
+                            mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use)  # warm
+                            flush.zero_()
+                            _, dists = mr.mrpt_query_ex(index, Q, k, v, n_trees=T_use, stage_ms=stage)
+                            kth = gt_d[:, k - 1:k].float()
+                            rec = float(((dists <= kth * (1 + 1e-5)) & torch.isfinite(dists)).sum()) / (m * k)
+                            pts[k].append(dict(T=T_use, l=l, v=v, recall=round(rec, 4),
+                                               qps=round(m / (float(stage[3]) / 1e3), 1)))
+                index.close()
+            out[name] = {}
+            for k in ks:
+                ok = [p for p in pts[k] if p["recall"] >= 0.9]
+                out[name][f"k={k}"] = {"best_at_recall_0.9": max(ok, key=lambda p: p["qps"]) if ok else None,
+                                       "front": _front(pts[k])}
+        return out
+
+    result = {"metric": "Pareto fronts: queries/s vs tie-aware recall@k (device time, L2 flushed)",
+              "T_grid": T_grid, "data": "synthetic"}
+    X_np, Q_np = workloads.mnist_like(60000, 10000, seed=0)
+    X, Q = torch.from_numpy(X_np).to(dev), torch.from_numpy(Q_np).to(dev)
+    variants = [("MRPT (a = 1/sqrt(d), voting)", 0.0, 0, range(1, 11)),
+                ("MRPT, exactly ceil(a d) nonzeros per vector", 0.0, 1, range(1, 11)),
+                ("sparse RP trees, no voting (v = 1)", 0.0, 0, (1,)),
+                ("dense RP trees (a = 1), no voting (v = 1)", 1.0, 0, (1,))]
+    result["mnist-like 60000x784, 10000 queries"] = sweep(X, Q, variants, (6, 7, 8, 9), (1, 10, 100))
+    del X, Q
+    X_np, Q_np = workloads.unit_gaussian(50000, 4096, 1000, seed=0)
+    X, Q = torch.from_numpy(X_np).to(dev), torch.from_numpy(Q_np).to(dev)
+    result["Random: unit-length N(0, I) 50000x4096, 1000 queries"] = sweep(
+        X, Q, [("MRPT (a = 1/sqrt(d), voting)", 0.0, 0, range(1, 11))], (6, 8, 10), (10,))
+    print(json.dumps(result), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,7 +714,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--build-shapes", type=int, default=2, help="build workload: how many shapes")
-    ap.add_argument("--workload", choices=["batch", "stream", "build"], default="batch",
+    ap.add_argument("--workload", choices=["batch", "stream", "build", "pareto"], default="batch",
                     help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
     ap.add_argument("--stream-queries", type=int, default=100000)
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp8"], default="auto",
@@ -653,6 +734,8 @@ def main():
         run_stream(args)
     elif args.workload == "build":
         run_build(args)
+    elif args.workload == "pareto":
+        run_pareto(args)
     else:
         run_gpu(args)
 

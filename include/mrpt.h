@@ -85,6 +85,32 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
                uint64_t seed, mrpt_index **out);
 
 /*
+ * mrpt_build_ex -- mrpt_build with options (opts may be NULL: the defaults).
+ *
+ *   sparsity  how each level's random vector gets its nonzeros:
+ *     MRPT_SPARSITY_BERNOULLI (0, default): component i is nonzero with
+ *       probability density (Sec. II-B), as in mrpt_build.
+ *     MRPT_SPARSITY_FIXED (1): exactly ceil(density * d) nonzeros per vector
+ *       (at least 1, at most d; density * d is taken with a relative
+ *       allowance of 1e-6, since density is a float) -- the variant in the
+ *       footnote of Sec. II-B, an ablation of Table III.  The nonzero
+ *       dimensions are those with the smallest (first draw, dimension), the
+ *       first draw being the one the Bernoulli rule compares with density,
+ *       so the set is a uniformly random subset; values are the same N(0,1)
+ *       draws as in the Bernoulli rule.
+ * Errors: those of mrpt_build; INVALID_ARG for an unknown sparsity.
+ */
+#define MRPT_SPARSITY_BERNOULLI 0
+#define MRPT_SPARSITY_FIXED 1
+
+typedef struct mrpt_build_opts {
+    int32_t sparsity;
+} mrpt_build_opts;
+
+int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
+                  uint64_t seed, const mrpt_build_opts *opts, mrpt_index **out);
+
+/*
  * mrpt_query -- Algorithm 4 (with Algorithm 3 per tree) for m queries.
  *
  *   Q          m x d float32 queries, host or device.

@@ -52,7 +52,10 @@ ABI_SYMBOLS = (
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
     "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
     "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free", "mrpt_save", "mrpt_load",
+    "mrpt_build_ex",
 )
+MRPT_SPARSITY_BERNOULLI = 0
+MRPT_SPARSITY_FIXED = 1
 MRPT_PREC_FP32 = 0
 MRPT_PREC_BF16 = 1
 MRPT_PREC_FP8 = 2
@@ -63,6 +66,10 @@ class MRPTError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[{code}] {msg}")
         self.code = code
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("sparsity", ctypes.c_int32)]
 
 
 class QueryOpts(ctypes.Structure):
@@ -121,6 +128,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_build.restype = ctypes.c_int
         lib.mrpt_build.argtypes = [vp, i64, i32, i32, i32, f32, ctypes.c_uint64,
                                    ctypes.POINTER(vp)]
+        lib.mrpt_build_ex.restype = ctypes.c_int
+        lib.mrpt_build_ex.argtypes = [vp, i64, i32, i32, i32, f32, ctypes.c_uint64,
+                                      ctypes.POINTER(BuildOpts), ctypes.POINTER(vp)]
         lib.mrpt_query.restype = ctypes.c_int
         lib.mrpt_query.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         lib.mrpt_query_ex.restype = ctypes.c_int
@@ -254,15 +264,19 @@ class Index:
             pass
 
 
-def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0) -> Index:
+def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0,
+               sparsity: int = MRPT_SPARSITY_BERNOULLI) -> Index:
     """Algorithm 1: grow T trees of depth l over the rows of ``data`` (torch
-    tensor on the GPU or the host, or a numpy array)."""
+    tensor on the GPU or the host, or a numpy array).  sparsity selects the
+    random vectors' nonzeros (mrpt_build_ex): MRPT_SPARSITY_BERNOULLI or
+    MRPT_SPARSITY_FIXED (exactly ceil(density * d) per vector)."""
     lib = load_library()
     data = _as_f32(data)
     n, d = data.shape
     h = ctypes.c_void_p()
-    _check(lib.mrpt_build(_ptr(data), n, d, T, l, float(density), seed & (2**64 - 1),
-                          ctypes.byref(h)))
+    opts = BuildOpts(int(sparsity))
+    _check(lib.mrpt_build_ex(_ptr(data), n, d, T, l, float(density), seed & (2**64 - 1),
+                             ctypes.byref(opts), ctypes.byref(h)))
     if _is_torch(data) and data.is_cuda:
         # mrpt_build copies the data; keep the source alive until it returns (it is synchronous)
         pass

@@ -223,9 +223,19 @@ int mrpt_debug_fail_alloc_after(int32_t after) {
 
 int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
                uint64_t seed, mrpt_index **out) {
+    return mrpt_build_ex(data, n, d, T, l, density, seed, nullptr, out);
+}
+
+int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
+                  uint64_t seed, const mrpt_build_opts *opts, mrpt_index **out) {
     clear_error();
     if (!out) {
         set_error("mrpt_build: out is NULL");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    const int32_t sparsity = opts ? opts->sparsity : MRPT_SPARSITY_BERNOULLI;
+    if (sparsity != MRPT_SPARSITY_BERNOULLI && sparsity != MRPT_SPARSITY_FIXED) {
+        set_error("mrpt_build: unknown sparsity " + std::to_string(sparsity));
         return MRPT_ERR_INVALID_ARG;
     }
     *out = nullptr;
@@ -283,7 +293,7 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
     }
 
     // ---- random matrix (Algorithm 1, Sec. II-B/II-C)
-    generate_random_matrix(T, l, d, density, seed, idx->h_col_off, idx->h_dim, idx->h_val);
+    generate_random_matrix(T, l, d, density, seed, sparsity, idx->h_col_off, idx->h_dim, idx->h_val);
     idx->nnz = int64_t(idx->h_dim.size());
     const size_t cbytes = idx->h_col_off.size() * sizeof(int32_t);
     const size_t nbytes = size_t(idx->nnz) * sizeof(int32_t);

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "mrpt_internal.cuh"
@@ -42,27 +43,55 @@ inline double u53_open_closed(uint64_t x) { return (double(x >> 11) + 1.0) * 0x1
 
 }  // namespace
 
+int32_t fixed_nonzeros(float density, int32_t d) {
+    // ceil(a d) in [1, d]; a arrives as a float, so a relative allowance of
+    // 1e-6 keeps e.g. float(1/sqrt(784)) * 784 = 28.0000013 at 28
+    double k = std::ceil(double(density) * double(d) * (1.0 - 1e-6));
+    k = std::min(std::max(k, 1.0), double(d));
+    return int32_t(k);
+}
+
 void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
-                            std::vector<int32_t> &col_off, std::vector<int32_t> &dim,
-                            std::vector<float> &val) {
+                            int32_t sparsity, std::vector<int32_t> &col_off,
+                            std::vector<int32_t> &dim, std::vector<float> &val) {
     const double a = double(density);
     const double tau = 2.0 * 3.14159265358979323846;
     const int64_t ncols = int64_t(T) * l;
+    const bool fixed = sparsity == MRPT_SPARSITY_FIXED;
+    const int32_t k = fixed ? fixed_nonzeros(density, d) : 0;
     col_off.assign(size_t(ncols + 1), 0);
     dim.clear();
     val.clear();
-    dim.reserve(size_t(double(ncols) * d * a * 1.2 + 16));
+    dim.reserve(fixed ? size_t(ncols * k) : size_t(double(ncols) * d * a * 1.2 + 16));
     val.reserve(dim.capacity());
+    std::vector<std::pair<double, int32_t>> draws(fixed ? size_t(d) : 0);
+    std::vector<int32_t> pick(fixed ? size_t(k) : 0);
+    auto normal_at = [&](uint64_t ctr) {
+        const double u1 = u53_open_closed(splitmix64_at(seed, ctr + 1));
+        const double u2 = u53_closed_open(splitmix64_at(seed, ctr + 2));
+        return float(std::sqrt(-2.0 * std::log(u1)) * std::cos(tau * u2));
+    };
     for (int64_t c = 0; c < ncols; ++c) {
         col_off[size_t(c)] = int32_t(dim.size());
         const uint64_t base = 3ULL * uint64_t(c) * uint64_t(d);
+        if (fixed) {
+            // the k dimensions with the smallest (first draw, dimension)
+            for (int32_t i = 0; i < d; ++i)
+                draws[size_t(i)] = {u53_closed_open(splitmix64_at(seed, base + 3ULL * uint64_t(i))), i};
+            std::nth_element(draws.begin(), draws.begin() + (k - 1), draws.end());
+            for (int32_t r = 0; r < k; ++r) pick[size_t(r)] = draws[size_t(r)].second;
+            std::sort(pick.begin(), pick.end());
+            for (int32_t i : pick) {
+                dim.push_back(i);
+                val.push_back(normal_at(base + 3ULL * uint64_t(i)));
+            }
+            continue;
+        }
         for (int32_t i = 0; i < d; ++i) {
             const uint64_t ctr = base + 3ULL * uint64_t(i);
             if (u53_closed_open(splitmix64_at(seed, ctr)) < a) {
-                const double u1 = u53_open_closed(splitmix64_at(seed, ctr + 1));
-                const double u2 = u53_closed_open(splitmix64_at(seed, ctr + 2));
                 dim.push_back(i);
-                val.push_back(float(std::sqrt(-2.0 * std::log(u1)) * std::cos(tau * u2)));
+                val.push_back(normal_at(ctr));
             }
         }
     }

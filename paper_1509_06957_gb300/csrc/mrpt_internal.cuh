@@ -101,10 +101,14 @@ namespace mrpt {
 // ------------------------------------------------------ build (mrpt_build.cu)
 
 // Random matrix of Algorithm 1 on the host (counter-based SplitMix64 +
-// Box-Muller); compressed columns, column c = t*l + j.
+// Box-Muller); compressed columns, column c = t*l + j.  sparsity is
+// MRPT_SPARSITY_BERNOULLI or MRPT_SPARSITY_FIXED (see mrpt_build_ex).
 void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
-                            std::vector<int32_t> &col_off, std::vector<int32_t> &dim,
-                            std::vector<float> &val);
+                            int32_t sparsity, std::vector<int32_t> &col_off,
+                            std::vector<int32_t> &dim, std::vector<float> &val);
+
+// Nonzeros per vector of MRPT_SPARSITY_FIXED: ceil(density * d) in [1, d].
+int32_t fixed_nonzeros(float density, int32_t d);
 
 // Ids whose 8-bit vote counters fit in shared memory at once (64 KB).
 constexpr int64_t VOTE_CHUNK_IDS = 65536;

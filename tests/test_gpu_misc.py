@@ -1,6 +1,7 @@
 """GPU: index save/load, the paper's fully specified "Random" workload
-(unit-length N(0, I) vectors, d = 4096, Sec. IV-A) and the dense
-(a = 1, classic RP tree) ablation, each against the oracle."""
+(unit-length N(0, I) vectors, d = 4096, Sec. IV-A), the dense (a = 1,
+classic RP tree) ablation and the fixed-count sparse vectors of the
+Sec. II-B footnote, each against the oracle."""
 import os
 
 import numpy as np
@@ -23,11 +24,11 @@ def mr():
     return m
 
 
-def _check(mr, X, Q, T, l, k, v, density, seed, idx=None):
+def _check(mr, X, Q, T, l, k, v, density, seed, idx=None, sparsity=0):
     own = idx is None
     if own:
-        idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, density, seed)
-    ref = oracle.grow_trees(X, T, l, density, seed)
+        idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, density, seed, sparsity=sparsity)
+    ref = oracle.grow_trees(X, T, l, density, seed, sparsity=sparsity)
     check_index_parity(idx, mr, ref)
     gi, gd = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v)
     torch.cuda.synchronize()
@@ -72,3 +73,26 @@ def test_dense_classic_rp_trees(mr):
     """a = 1: classic dense RP trees with one vector per level."""
     X, Q = workloads.gaussian_mixture(2000, 48, 20, n_centres=10, seed=6)
     _check(mr, X, Q, 5, 4, 10, 2, 1.0, 4)
+
+
+@pytest.mark.parametrize("d,density", [(784, 0.0), (128, 0.0), (37, 0.3)])
+def test_fixed_count_sparse_vectors(mr, d, density):
+    """Exactly ceil(a d) nonzeros per vector (mrpt_build_ex, sparsity
+    FIXED): random matrix, splits, leaves and answers equal the oracle's."""
+    if d == 784:
+        X, Q = workloads.mnist_like(3000, 40, seed=4)
+    else:
+        X, Q = workloads.gaussian_mixture(2500, d, 40, n_centres=12, seed=4)
+    a = density if density > 0 else float(np.float32(1.0 / np.sqrt(d)))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 12, 6, a, 21, sparsity=mr.MRPT_SPARSITY_FIXED)
+    k_nz = oracle.fixed_count(a, d)
+    assert np.all(np.diff(mr.mrpt_export(idx, "R_COL_OFF")) == k_nz)
+    _check(mr, X, Q, 12, 6, 10, 3, a, 21, idx=idx, sparsity=oracle.SPARSITY_FIXED)
+    idx.close()
+
+
+def test_unknown_sparsity_is_rejected(mr):
+    X = np.random.default_rng(0).standard_normal((64, 6)).astype(np.float32)
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_build(X, 2, 2, 0.5, 0, sparsity=7)
+    assert e.value.code == mr.MRPT_ERR_INVALID_ARG
