@@ -135,6 +135,9 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->status);
     for (cudaEvent_t &ev : idx->ev)
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t &ev : idx->pev)
+        if (ev) cudaEventDestroy(ev);
+    if (idx->copy_stream) cudaStreamDestroy(idx->copy_stream);
     idx->q_leaf.release();
     idx->q_stage.release();
     idx->o_stage.release();
@@ -389,6 +392,11 @@ int mrpt_info(const mrpt_index *idx, mrpt_index_info *info) {
     return MRPT_OK;
 }
 
+// Host queries in batches of at least this many are copied in chunks, each
+// chunk routed as soon as it has arrived, so the copy overlaps routing.
+constexpr int kPipeChunks = 4;
+constexpr int64_t kPipeMinQueries = 8192;
+
 int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
                   const mrpt_query_opts *opts, int32_t *out_ids, float *out_dists) {
     clear_error();
@@ -435,11 +443,14 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
 
     // ---- inputs
     const float *Qd = Q;
-    if (!is_device_ptr(Q)) {
+    const bool q_host = !is_device_ptr(Q);
+    const bool chunked_in = q_host && m >= kPipeMinQueries &&
+                            (!opts || (!opts->proj && !opts->leaf && !opts->stage_ms));
+    if (q_host) {
         any_host = true;
         const size_t qb = size_t(m) * size_t(idx->d) * sizeof(float);
         if ((rc = idx->q_stage.ensure(qb, "query staging"))) return rc;
-        MRPT_CUDA_TRY(cudaMemcpyAsync(idx->q_stage.ptr, Q, qb, cudaMemcpyHostToDevice, s));
+        if (!chunked_in) MRPT_CUDA_TRY(cudaMemcpyAsync(idx->q_stage.ptr, Q, qb, cudaMemcpyHostToDevice, s));
         Qd = static_cast<const float *>(idx->q_stage.ptr);
     }
     // ---- outputs (device buffers in place, host buffers staged)
@@ -513,6 +524,33 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         cand_carve(lay, static_cast<char *>(idx->q_cand.ptr), m, ql);
     }
 
+    if (chunked_in) {
+        // copy the queries in chunks on a second stream; route each chunk
+        // on the index's stream as soon as it has arrived
+        if (!idx->copy_stream) MRPT_CUDA_TRY(cudaStreamCreateWithFlags(&idx->copy_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : idx->pev)
+            if (!e) MRPT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaStream_t cs = idx->copy_stream;
+        MRPT_CUDA_TRY(cudaEventRecord(idx->pev[0], s));  // after work already queued
+        MRPT_CUDA_TRY(cudaStreamWaitEvent(cs, idx->pev[0], 0));
+        const int64_t mc = (m + kPipeChunks - 1) / kPipeChunks;
+        const size_t row = size_t(idx->d) * sizeof(float);
+        int c = 0;
+        for (int64_t q0 = 0; q0 < m; q0 += mc, ++c) {
+            const int64_t mq = std::min(mc, m - q0);
+            char *dst = static_cast<char *>(idx->q_stage.ptr) + size_t(q0) * row;
+            MRPT_CUDA_TRY(cudaMemcpyAsync(dst, reinterpret_cast<const char *>(Q) + size_t(q0) * row,
+                                          size_t(mq) * row, cudaMemcpyHostToDevice, cs));
+            MRPT_CUDA_TRY(cudaEventRecord(idx->pev[1 + c], cs));
+            MRPT_CUDA_TRY(cudaStreamWaitEvent(s, idx->pev[1 + c], 0));
+            QueryLaunch qc = ql;
+            qc.Q = reinterpret_cast<const float *>(dst);
+            qc.m = mq;
+            qc.leaf = ql.leaf + q0 * n_trees;
+            if ((rc = launch_route_only(idx, qc))) return rc;
+        }
+        ql.routed = true;
+    }
     if ((rc = launch_query(idx, ql))) return rc;
 
     // ---- copy staged results back

@@ -94,6 +94,10 @@ struct mrpt_index {
 
     int64_t device_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (created on first use)
+    // host-buffer queries in pipelined chunks: a copy stream and per-chunk
+    // events (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pev[16] = {};
 };
 
 namespace mrpt {
@@ -182,9 +186,13 @@ struct QueryLaunch {
     cudaStream_t stream;   // stream of the launches (plans capture on their own)
     bool use_stream;       // take `stream` instead of the index's stream
     const QueryRecord *rec;  // plan mode: batch read on the device (m <= ql.m)
+    bool routed;           // ql.leaf is already filled (routing skipped)
 };
 
 int launch_query(mrpt_index *idx, const QueryLaunch &ql);
+
+// Routing alone (projection and descent) for ql.m queries into ql.leaf.
+int launch_route_only(mrpt_index *idx, const QueryLaunch &ql);
 
 // launch_query with caller-supplied scratch: ql.leaf holds the m x n_trees
 // leaf-of-query table and `work` the work counter.

@@ -20,6 +20,10 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
 
 #include "mrpt_internal.cuh"
 
@@ -1719,17 +1723,51 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
 
 namespace {
 
+// Blocks per SM of `func` at `threads` threads and `smem` bytes of dynamic
+// shared memory, and the SM count, raising the kernel's shared-memory limit
+// first when needed.  The driver queries behind this cost microseconds each,
+// which adds up for small batches, so results are kept per (device, kernel,
+// threads, bytes).
+cudaError_t launch_shape(const void *func, int threads, size_t smem, int device, int *per_sm, int *sms) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> occ;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    static std::map<int, int> sm_count;
+    std::lock_guard<std::mutex> guard(mu);
+    cudaError_t e;
+    auto sc = sm_count.find(device);
+    if (sc == sm_count.end()) {
+        int c = 0;
+        if ((e = cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+        sc = sm_count.emplace(device, c).first;
+    }
+    *sms = sc->second;
+    const auto key = std::make_tuple(device, func, threads, smem);
+    const auto hit = occ.find(key);
+    if (hit != occ.end()) {
+        *per_sm = hit->second;
+        return cudaSuccess;
+    }
+    const auto lk = std::make_pair(device, func);
+    const auto li = limit.find(lk);
+    if (li == limit.end() || li->second < smem) {
+        if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+            return e;
+        limit[lk] = smem;
+    }
+    int p = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, func, threads, smem)) != cudaSuccess) return e;
+    occ[key] = p;
+    *per_sm = p;
+    return cudaSuccess;
+}
+
 template <int QB>
 cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
     const size_t smem = size_t(QB) * size_t(idx->d | 1) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_query_route<QB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query_route<QB>, 512, smem);
-    if (e != cudaSuccess) return e;
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    int per_sm = 0, sms = 0;
+    cudaError_t e = launch_shape(reinterpret_cast<const void *>(k_query_route<QB>), 512, smem, idx->device,
+                                 &per_sm, &sms);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (ql.m + QB - 1) / QB;
     const int64_t groups = (ql.n_trees + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM;
@@ -1754,13 +1792,9 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
     region = (region + 15) & ~size_t(15);
     smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 + size_t(3 * ql.n_trees) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_vote_search<KR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote_search<KR>, VS_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    cudaError_t e = launch_shape(reinterpret_cast<const void *>(k_vote_search<KR>), VS_THREADS, smem,
+                                 idx->device, &per_sm, &sms);
     if (e != cudaSuccess) return e;
     blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
     a = VoteSearchArgs{};
@@ -1840,12 +1874,9 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     const size_t smem = flat ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 12
                              : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
                                    size_t(4 * ql.n_trees + 1) * 4;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VE_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
+    cudaError_t e = launch_shape(reinterpret_cast<const void *>(kern), VE_THREADS, smem, idx->device, &per_sm,
+                                 &sms);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(sms) * std::max(per_sm, 1)));
     VoteEmitArgs a{};
@@ -1930,15 +1961,12 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.done = ql.done;
     a.part_d = ql.part_d;
     a.part_i = ql.part_i;
-    int sms = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device);
-    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    cudaError_t e;
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
-        e = cudaFuncSetAttribute(k_cand_knn<KR, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn<KR, RK>, CR_WARPS * 32, smem);
+        e = launch_shape(reinterpret_cast<const void *>(k_cand_knn<KR, RK>), CR_WARPS * 32, smem, idx->device,
+                         &per_sm, &sms);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((ql.m + CR_WARPS - 1) / CR_WARPS, int64_t(sms) * std::max(per_sm, 1)));
@@ -1947,10 +1975,8 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     }
     // float32 rows too long to stage: register path
     const size_t smem = size_t(CK_WARPS) * size_t(idx->dpad) * 4;
-    e = cudaFuncSetAttribute(k_cand_knn_regs<KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cand_knn_regs<KR>, CK_THREADS, smem);
+    e = launch_shape(reinterpret_cast<const void *>(k_cand_knn_regs<KR>), CK_THREADS, smem, idx->device, &per_sm,
+                     &sms);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(
         1, std::min<int64_t>((ql.m + CK_WARPS - 1) / CK_WARPS, int64_t(sms) * std::max(per_sm, 1)));
@@ -1980,6 +2006,13 @@ cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
 
 }  // namespace
 
+int launch_route_only(mrpt_index *idx, const QueryLaunch &ql) {
+    if (ql.m == 0) return MRPT_OK;
+    const cudaError_t e = launch_route_any(idx, ql, ql.use_stream ? ql.stream : idx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    return MRPT_OK;
+}
+
 int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     cudaStream_t s = ql.use_stream ? ql.stream : idx->stream;
     if (ql.m == 0) return MRPT_OK;
@@ -1989,8 +2022,10 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
             if (!idx->ev[i]) MRPT_CUDA_TRY(cudaEventCreate(&idx->ev[i]));
         MRPT_CUDA_TRY(cudaEventRecord(idx->ev[0], s));
     }
-    e = launch_route_any(idx, ql, s);
-    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    if (!ql.routed) {
+        e = launch_route_any(idx, ql, s);
+        if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    }
     if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[1], s));
     const int kr = (ql.k + 31) / 32;
     if (ql.path == 1 || ql.cand_list == nullptr) {

@@ -96,3 +96,22 @@ def test_unknown_sparsity_is_rejected(mr):
     with pytest.raises(mr.MRPTError) as e:
         mr.mrpt_build(X, 2, 2, 0.5, 0, sparsity=7)
     assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+
+
+def test_host_buffers_large_batch_chunked_upload(mr):
+    """Host queries in a batch of at least 8,192 are copied in chunks, each
+    routed as soon as it arrives; the answers equal those of device buffers."""
+    X, Q = workloads.mnist_like(6000, 9000, seed=6)
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 16, 5, 0.0, 3)
+    ids_d, dists_d = mr.mrpt_query(idx, torch.from_numpy(Q).cuda(), 10, 3)
+    ids_h, dists_h = mr.mrpt_query(idx, Q, 10, 3)
+    assert isinstance(ids_h, np.ndarray)
+    assert np.array_equal(dists_d.cpu().numpy().view(np.uint32), dists_h.view(np.uint32))
+    same = ids_d.cpu().numpy() == ids_h
+    # ids may differ only where distances tie
+    assert same.mean() > 0.999
+    mr.mrpt_add_lowp(idx, mr.MRPT_PREC_BF16)
+    a = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), 10, 3, precision=mr.MRPT_PREC_BF16, margin=8)
+    b = mr.mrpt_query_ex(idx, Q, 10, 3, precision=mr.MRPT_PREC_BF16, margin=8)
+    assert np.array_equal(a[1].cpu().numpy().view(np.uint32), b[1].view(np.uint32))
+    idx.close()
