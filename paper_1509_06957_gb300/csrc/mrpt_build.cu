@@ -535,6 +535,37 @@ __global__ void k_pad_leaves(const int32_t *__restrict__ leaf_ids, int64_t n, in
     }
 }
 
+// Each 128-id window of a padded leaf (the ids one warp votes with four
+// atomics, lane r taking window positions 4r..4r+3) is reordered by counter
+// bank ((id >> 2) mod 32, stable).  Atomic u of the warp then takes the ids
+// of ranks u, u+4, u+8, ... in bank order, so ids of one bank spread over
+// the four atomics instead of queueing in one.  One thread per window.
+__global__ void k_bank_order_windows(int32_t *__restrict__ leaf4, int32_t T,
+                                     const int32_t *__restrict__ off4, int64_t L, int64_t s4,
+                                     int32_t win) {
+    const int64_t total = int64_t(T) * L * win;
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+         g += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = g / (L * win);
+        const int64_t r = g - t * L * win;
+        const int64_t j = r / win;
+        const int32_t w = int32_t(r - j * win);
+        const int32_t len4 = off4[j + 1] - off4[j];
+        if (32 * w >= len4) continue;
+        const int32_t n4 = min(32, len4 - 32 * w);
+        int32_t *base = leaf4 + 4 * (t * s4 + off4[j] + 32 * w);
+        int32_t ids[128];
+        int32_t cnt[33];
+        for (int b = 0; b <= 32; ++b) cnt[b] = 0;
+        for (int e = 0; e < 4 * n4; ++e) {
+            ids[e] = base[e];
+            ++cnt[((ids[e] >> 2) & 31) + 1];
+        }
+        for (int b = 0; b < 32; ++b) cnt[b + 1] += cnt[b];
+        for (int e = 0; e < 4 * n4; ++e) base[cnt[(ids[e] >> 2) & 31]++] = ids[e];
+    }
+}
+
 }  // namespace
 
 int build_vote_layout(mrpt_index *idx) {
@@ -567,6 +598,14 @@ int build_vote_layout(mrpt_index *idx) {
                                                        idx->leaf_off4, L, s4, vote_sentinel(idx->n),
                                                        reinterpret_cast<int32_t *>(idx->leaf4));
         e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            const int64_t windows = int64_t(idx->T) * L * idx->vote_win;
+            const int wblocks = int(std::min<int64_t>((windows + 127) / 128, 152 * 16));
+            k_bank_order_windows<<<wblocks, 128, 0, idx->stream>>>(reinterpret_cast<int32_t *>(idx->leaf4),
+                                                                  idx->T, idx->leaf_off4, L, s4,
+                                                                  idx->vote_win);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "k_pad_leaves");
     }
