@@ -684,6 +684,11 @@ struct VoteSearchArgs {
     const int32_t *qlist;        // optional: process only these queries ...
     const uint32_t *qlist_len;   // ... this many of them (read on the device)
     const QueryRecord *rec;      // plan mode: Q, outputs and m of the batch
+    // vote layout (n <= 65,536): voted as in k_vote_flat
+    const int4 *leaf4;
+    const int32_t *leaf_off4;
+    int64_t s4;
+    int32_t sentinel;
 };
 
 // Per warp: a buffer of emitted candidates waiting for their distances.
@@ -757,8 +762,13 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
         for (int i = tid; i < a.dpad; i += VS_THREADS) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
         for (int t = tid; t < a.T_use; t += VS_THREADS) {
             const int32_t lf = a.leaf_of_q[qi * a.T_use + t];
-            cur[t] = a.leaf_off[lf];
-            lend[t] = a.leaf_off[lf + 1];
+            if (a.leaf4 != nullptr) {  // first 16-byte unit and length of the padded leaf
+                cur[t] = a.leaf_off4[lf];
+                lend[t] = a.leaf_off4[lf + 1] - cur[t];
+            } else {
+                cur[t] = a.leaf_off[lf];
+                lend[t] = a.leaf_off[lf + 1];
+            }
         }
         WarpTopK<KR> top;
         top.init();
@@ -786,7 +796,76 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
             __syncwarp();
         };
 
-        for (int64_t c0 = 0; c0 < a.n; c0 += CH_IDS) {
+        if (a.leaf4 != nullptr) {
+            // one id chunk, voted over the vote layout as in k_vote_flat: each
+            // warp takes its trees' 128-id windows; lanes past a leaf vote
+            // into their spare word; emitted ids are appended to the warp's
+            // buffer in lane order
+            const uint32_t cnt_s = smem_u32(cnt);
+            const uint32_t spare = cnt_s + 4u * uint32_t(a.cnt_words + 4 + lane);
+            {
+                uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+                for (int w = tid; w < (a.cnt_words >> 2); w += VS_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            __syncthreads();
+            int nb = 0;
+            for (int t = warp; t < a.T_use; t += VS_WARPS) {
+                const int4 *lp = a.leaf4 + int64_t(t) * a.s4 + cur[t];
+                const int32_t len4 = lend[t];
+                for (int w0 = 0; w0 < len4; w0 += 32) {
+                    const uint32_t ok = w0 + lane < len4 ? 1u : 0u;
+                    const int4 q = ldg4_if(lp + w0 + lane, ok);
+                    uint32_t em = vote4p(cnt_s, q, ok, spare, vm1);
+                    const int32_t e4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (e4[u] == a.sentinel) em &= ~(1u << u);
+                    if (__any_sync(0xffffffffu, em != 0u)) {
+                        const int mine = __popc(em);
+                        int incl = mine;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                        int pos = nb + incl - mine;
+                        unsigned long long base = 0;
+                        if (track) {
+                            if (lane == 0) base = atomicAdd(&s_total, (unsigned long long)tot);
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                        }
+                        int64_t slot = int64_t(base) + incl - mine;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if ((em >> u) & 1u) {
+                                mybuf[pos++] = e4[u];
+                                if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = e4[u];
+                                ++slot;
+                            }
+                        }
+                        nb += tot;
+                    }
+                    if (nb >= 64) {
+                        drain(nb);
+                        nb = 0;
+                    }
+                }
+            }
+            if (nb > 0) drain(nb);
+            __syncthreads();
+            if (a.dbg_votes != nullptr) {
+                for (int w = tid; w < int((a.n + 3) >> 2); w += VS_THREADS) {
+                    const uint32_t word = cnt[w];
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t id = 4 * int64_t(w) + b;
+                        if (id < a.n) a.dbg_votes[qi * a.n + id] = uint8_t((word >> (8 * b)) & 0xffu);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int64_t c0 = 0; a.leaf4 == nullptr && c0 < a.n; c0 += CH_IDS) {
             const int64_t wleft = (a.n - c0 + 3) >> 2;
             const int nwords = int(wleft < a.cnt_words ? wleft : int64_t(a.cnt_words));
             {
@@ -1789,7 +1868,8 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     const int64_t ids_chunk = idx->n < CH_IDS ? idx->n : CH_IDS;
     const int cnt_words = int(((ids_chunk + 3) / 4 + 3) & ~int64_t(3));
     const size_t merge_bytes = size_t(VS_WARPS) * KR * 32 * 8;
-    size_t region = std::max(size_t(cnt_words) * 4, merge_bytes);
+    // + the sentinel's word (and 3 unused) and a spare word per lane
+    size_t region = std::max(size_t(cnt_words + 36) * 4, merge_bytes);
     region = (region + 15) & ~size_t(15);
     smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 + size_t(3 * ql.n_trees) * 4;
     int per_sm = 0, sms = 0;
@@ -1819,6 +1899,10 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     a.work = work;
     a.cnt_words = cnt_words;
     a.region_bytes = int(region);
+    a.leaf4 = idx->leaf4;
+    a.leaf_off4 = idx->leaf_off4;
+    a.s4 = idx->vote_s4;
+    a.sentinel = vote_sentinel(idx->n);
     a.rec = ql.rec;
     return cudaSuccess;
 }
