@@ -1545,6 +1545,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     }
     extern __shared__ __align__(16) unsigned char csm[];
     __shared__ __align__(8) uint64_t s_bar[CR_WARPS][CR_MAX_RING];
+    __shared__ int32_t s_cid[CR_WARPS][64];  // candidate ids [cbase, cbase + 64) of the item
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int S = a.ring;
@@ -1602,41 +1603,42 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
             staged_q = qi;
         }
         const int32_t *clist = a.cand + qi * int64_t(a.capq) + lo;
-        // candidate ids f in [cbase, cbase + 64) live in two registers
+        // candidate ids f in [cbase, cbase + 64) in the warp's shared list
+        // (f stays below j + 1 + S < cbase + 32 + 17)
+        int32_t *cid = s_cid[warp];
         int cbase = 0;
-        int32_t ca = lane < c ? __ldg(clist + lane) : 0;
-        int32_t cb = 32 + lane < c ? __ldg(clist + 32 + lane) : 0;
-        auto id_at = [&](int f) -> int32_t {
-            const int r = f - cbase;
-            const int32_t va = __shfl_sync(0xffffffffu, ca, r & 31);
-            const int32_t vb = __shfl_sync(0xffffffffu, cb, r & 31);
-            return r < 32 ? va : vb;
-        };
-        auto issue = [&](int f, int slot) {
-            const int32_t id = id_at(f);
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&bar[slot], row_bytes);
-                bulk_copy_g2s(ring + size_t(slot) * row_bytes, Xb + size_t(id) * row_bytes, row_bytes,
-                              &bar[slot]);
-            }
-            inflight |= 1u << slot;
+        __syncwarp();
+        cid[lane] = lane < c ? __ldg(clist + lane) : 0;
+        cid[32 + lane] = 32 + lane < c ? __ldg(clist + 32 + lane) : 0;
+        __syncwarp();
+        // lane 0 starts the copy of candidate f's row into `slot`
+        auto copy_row = [&](int f, int slot) {
+            const int32_t id = cid[f - cbase];
+            mbar_arrive_expect_tx(&bar[slot], row_bytes);
+            bulk_copy_g2s(ring + size_t(slot) * row_bytes, Xb + size_t(id) * row_bytes, row_bytes, &bar[slot]);
         };
         const int prime = c < S ? c : S;
-        for (int f = 0; f < prime; ++f) issue(f, f);
+        if (lane == 0)
+            for (int f = 0; f < prime; ++f) copy_row(f, f);
+        inflight |= (1u << prime) - 1u;
         __syncwarp();
         WarpTopK<KR> top;
         top.init();
         int slot = 0;
         for (int j = 0; j < c; j += 2) {
             if (j - cbase >= 32) {
+                const int32_t hi = cid[32 + lane];
+                const int32_t nx = cbase + 64 + lane < c ? __ldg(clist + cbase + 64 + lane) : 0;
+                __syncwarp();
+                cid[lane] = hi;
+                cid[32 + lane] = nx;
                 cbase += 32;
-                ca = cb;
-                cb = cbase + 32 + lane < c ? __ldg(clist + cbase + 32 + lane) : 0;
+                __syncwarp();
             }
             const bool two = j + 1 < c;
             const int slot1 = (slot + 1 == S) ? 0 : slot + 1;
-            const int32_t id0 = id_at(j);
-            const int32_t id1 = two ? id_at(j + 1) : id0;
+            const int32_t id0 = cid[j - cbase];
+            const int32_t id1 = two ? cid[j + 1 - cbase] : id0;
             // warp-uniform outcome of the bounded waits
             bool ok = mbar_wait(&bar[slot], (parity >> slot) & 1u);
             if (two) ok = mbar_wait(&bar[slot1], (parity >> slot1) & 1u) && ok;
@@ -1668,8 +1670,14 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
                                            reinterpret_cast<const float4 *>(ring + size_t(two ? slot1 : slot) * row_bytes),
                                            q4, nv4, lane, dd0, dd1);
             __syncwarp();  // every lane has read both slots
-            if (j + S < c) issue(j + S, slot);
-            if (two && j + 1 + S < c) issue(j + 1 + S, slot1);
+            {
+                const bool n0 = j + S < c, n1 = two && j + 1 + S < c;
+                if (lane == 0) {
+                    if (n0) copy_row(j + S, slot);
+                    if (n1) copy_row(j + 1 + S, slot1);
+                }
+                inflight |= (n0 ? 1u << slot : 0u) | (n1 ? 1u << slot1 : 0u);
+            }
             top.insert(dd0, id0, k, lane);
             if (two) top.insert(dd1, id1, k, lane);
             slot = two ? ((slot1 + 1 == S) ? 0 : slot1 + 1) : slot1;
