@@ -1534,7 +1534,9 @@ constexpr int CR_WARPS = 4;
 constexpr int CR_MAX_RING = 16;
 
 // RK: 0 float32 rows, 1 bfloat16 rows, 2 e4m3 rows with a per-row scale.
-template <int KR, int RK>
+// SR > 0 fixes the ring to SR slots at compile time (slot indices and
+// parity bits then fold to constants); SR = 0 takes a.ring.
+template <int KR, int RK, int SR>
 __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0) {
     CandKnnArgs a = a0;
     if (a.rec != nullptr) {
@@ -1548,7 +1550,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     __shared__ int32_t s_cid[CR_WARPS][64];  // candidate ids [cbase, cbase + 64) of the item
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int S = a.ring;
+    const int S = SR > 0 ? SR : a.ring;
     const uint32_t row_bytes = a.row_bytes;
     unsigned char *wbase = csm + size_t(warp) * (size_t(a.dpad) * 4 + size_t(S) * row_bytes);
     float *qv = reinterpret_cast<float *>(wbase);
@@ -2057,12 +2059,13 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     cudaError_t e;
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
-        e = launch_shape(reinterpret_cast<const void *>(k_cand_knn<KR, RK>), CR_WARPS * 32, smem, idx->device,
-                         &per_sm, &sms);
+        // the default two-slot ring of k <= 64 as a compile-time constant
+        auto kern = (ring == 2 && KR <= 2) ? k_cand_knn<KR, RK, 2> : k_cand_knn<KR, RK, 0>;
+        e = launch_shape(reinterpret_cast<const void *>(kern), CR_WARPS * 32, smem, idx->device, &per_sm, &sms);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((ql.m + CR_WARPS - 1) / CR_WARPS, int64_t(sms) * std::max(per_sm, 1)));
-        k_cand_knn<KR, RK><<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
+        kern<<<unsigned(blocks), CR_WARPS * 32, smem, s>>>(a);
         return cudaGetLastError();
     }
     // float32 rows too long to stage: register path
