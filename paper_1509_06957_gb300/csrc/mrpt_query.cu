@@ -43,7 +43,7 @@ namespace mrpt {
 constexpr int ROUTE_TREES_PER_ITEM = 16;
 
 template <int QB>
-__global__ void __launch_bounds__(512) k_query_route(
+__global__ void __launch_bounds__(512, 2) k_query_route(
     const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
     const int2 *__restrict__ rcol, const int2 *__restrict__ dv,
     const float *__restrict__ split, int32_t *__restrict__ leaf,
@@ -1373,29 +1373,35 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
                 }
             }
         };
-        // warps claim two windows at a time from a shared counter (so they
-        // finish together); both loads are in flight before either votes,
+        // warps claim four windows at a time from a shared counter (so they
+        // finish together); all four loads are in flight before any votes,
         // and a window past W votes nothing
         for (;;) {
             int i = 0;
-            if (lane == 0) i = atomicAdd(&s_win, 2);
+            if (lane == 0) i = atomicAdd(&s_win, 4);
             i = __shfl_sync(0xffffffffu, i, 0);
             if (i >= W) break;
             int t = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32), k = i - t * K;
-            const int32_t ja = k * 32 + lane;
-            const uint32_t oka = ja < slen[t] ? 1u : 0u;
-            const int4 qa = ldg4_if(a.leaf4 + sbase[t] + ja, oka);
-            k = k + 1 == K ? 0 : k + 1;
-            t = k == 0 ? t + 1 : t;
-            const int tb = t < T ? t : T - 1;
-            const int32_t jb = k * 32 + lane;
-            const uint32_t okb = (i + 1 < W && jb < slen[tb]) ? 1u : 0u;
-            const int4 qb = ldg4_if(a.leaf4 + sbase[tb] + jb, okb);
-            const uint32_t ea = vote4p(cnt_s, qa, oka, spare, vm1);
-            const uint32_t eb = vote4p(cnt_s, qb, okb, spare, vm1);
-            if ((ea | eb) != 0u) {
-                emit(qa, ea);
-                emit(qb, eb);
+            int4 q[4];
+            uint32_t ok[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int tc = t < T ? t : T - 1;
+                const int32_t j = k * 32 + lane;
+                ok[r] = (i + r < W && j < slen[tc]) ? 1u : 0u;
+                q[r] = ldg4_if(a.leaf4 + sbase[tc] + j, ok[r]);
+                k = k + 1 == K ? 0 : k + 1;
+                t = k == 0 ? t + 1 : t;
+            }
+            uint32_t em[4], any = 0u;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                em[r] = vote4p(cnt_s, q[r], ok[r], spare, vm1);
+                any |= em[r];
+            }
+            if (any != 0u) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) emit(q[r], em[r]);
             }
         }
         if (qn >= 0 && tid < T) {
