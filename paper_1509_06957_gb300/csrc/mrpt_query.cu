@@ -1,18 +1,22 @@
-// Query phase (Sec. III, Algorithms 3-4) on sm_103a.
+// Query phase (Sec. III, Algorithms 3-4) on sm_103a.  A batch runs
 //
 //   k_query_route   p = q^T R for every tree and level (Algorithm 3), then
-//                   the descent p[level] <= split -> left.  A block stages up
-//                   to 32 queries in shared memory; one thread per (query,
-//                   tree), lanes of a warp share trees.
-//   k_vote_search   persistent blocks take queries from an atomic counter.
-//                   Per query: 8-bit vote counters for a chunk of point ids
-//                   in shared memory, incremented by warp-wide passes over
-//                   each tree's leaf (Algorithm 4's vote loop); points with
-//                   at least v votes are compacted into a candidate buffer
-//                   (S of Sec. III-A); a warp per candidate computes the
-//                   float32 squared distance with 128-bit loads and keeps a
-//                   per-warp sorted top-k in registers; the warps' lists are
-//                   merged by rank (knn(q, k, S) of Algorithm 4).
+//                   the descent p[level] <= split -> left.  A block stages
+//                   up to 32 queries in shared memory; one thread per
+//                   (query, tree), lanes of a warp share trees.
+//   k_vote_flat     (n <= 65,536) votes (Algorithm 4's loop) over the
+//                   padded leaf layout: 8-bit counters in shared memory, four
+//                   ids per lane per 16-byte load, one block of PTX per four
+//                   votes; a point enters S (Sec. III-A) when its count
+//                   reaches v and is appended to the query's candidate list.
+//   k_vote_emit     the same for larger n, in chunks of 65,536 ids.
+//   k_cand_knn      exact distances of the listed candidates, rows streamed
+//                   into a per-warp ring by bulk copies, and the per-warp
+//                   sorted top-k (knn(q, k, S) of Algorithm 4).
+//   k_vote_search   the one-kernel variant (votes, then distances of the
+//                   ids each warp emitted, then a merge of the warps'
+//                   lists); it also answers queries whose S overflows the
+//                   list capacity.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -508,29 +512,6 @@ __device__ __forceinline__ float smem_row_sq_dist(const float4 *row, const float
         a = sq_acc2(make_float2(q.z, q.w), make_float2(x.z, x.w), a);
     }
     return warp_sum(a.x + a.y);
-}
-
-// The same for a bfloat16 row: 8 components per 16-byte load, widened to
-// float exactly, differences and accumulation in float32.
-__device__ __forceinline__ float smem_row_sq_dist_bf16(const uint4 *row, const float4 *q4, int nv8,
-                                                       int lane) {
-    float a0 = 0.f, a1 = 0.f;
-    for (int j = lane; j < nv8; j += 32) {
-        const uint4 raw = row[j];
-        const float4 qa = q4[2 * j];
-        const float4 qb = q4[2 * j + 1];
-        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-        const float qs[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float lo = __uint_as_float(w[h] << 16);
-            const float hi = __uint_as_float(w[h] & 0xffff0000u);
-            const float d0 = qs[2 * h] - lo, d1 = qs[2 * h + 1] - hi;
-            a0 = __fmaf_rn(d0, d0, a0);
-            a1 = __fmaf_rn(d1, d1, a1);
-        }
-    }
-    return warp_sum(a0 + a1);
 }
 
 // Two staged rows against the staged query at once: one query load feeds
@@ -1564,7 +1545,6 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     uint64_t *bar = s_bar[warp];
     const float4 *q4 = reinterpret_cast<const float4 *>(qv);
     const unsigned char *Xb = reinterpret_cast<const unsigned char *>(a.rows);
-    const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
     const int nv4 = a.dpad >> 2;
     const int k = a.k;
     if (lane == 0) {
