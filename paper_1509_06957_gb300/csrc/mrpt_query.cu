@@ -37,14 +37,15 @@ namespace mrpt {
 
 // One thread per (query, tree): lane = query (QB = 32 queries per tile, or
 // QB < 32 queries x 32/QB trees per warp when d is large).  Work items are
-// (query tile, group of ROUTE_TREES_PER_ITEM trees); a persistent block
-// takes a contiguous range of items, so it stages a query tile once and
-// walks its tree groups.  All lanes that share a tree read the same
-// nonzeros as (dim, value bits) pairs, two per 16-byte broadcast load, and take their query's
-// component from shared memory (odd row stride: no bank conflicts).  Each
-// projection is an fmaf chain in ascending dimension from +0.0f, followed by
-// the descent p <= split -> left (Algorithm 3).
-constexpr int ROUTE_TREES_PER_ITEM = 16;
+// (query tile, group of 16 * 32/QB trees, one per warp and lane group); a
+// persistent block takes a contiguous range of items, so it stages a query
+// tile once and walks its tree groups.  All lanes that share a tree read the
+// same nonzeros as (dim, value bits) pairs, two per 16-byte broadcast load,
+// and take their query's component from shared memory (odd row stride: no
+// bank conflicts).  Each projection is an fmaf chain in ascending dimension
+// from +0.0f, followed by the descent p <= split -> left (Algorithm 3).
+template <int QB>
+__host__ __device__ constexpr int route_tpi() { return 16 * (32 / QB); }
 
 template <int QB>
 __global__ void __launch_bounds__(512, 2) k_query_route(
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(512, 2) k_query_route(
     if (rec != nullptr) {
         Q = rec->Q;
         m = rec->m;
-        n_items = ((m + QB - 1) / QB) * ((T_use + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM);
+        n_items = ((m + QB - 1) / QB) * ((T_use + route_tpi<QB>() - 1) / route_tpi<QB>());
     }
     constexpr int G = 32 / QB;
     const int lane = threadIdx.x & 31;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(512, 2) k_query_route(
     const float *qrow = qs + qq * stride;
     const int64_t inner = L - 1;
     const int ncols = T_use * l;
-    const int groups = (T_use + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM;
+    const int groups = (T_use + route_tpi<QB>() - 1) / route_tpi<QB>();
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
     // contiguous item range of this block
     const int64_t per = n_items / gridDim.x, extra = n_items % gridDim.x;
@@ -114,8 +115,8 @@ __global__ void __launch_bounds__(512, 2) k_query_route(
             staged = tile;
         }
         const bool live = qq < nq;
-        const int t_begin = grp * ROUTE_TREES_PER_ITEM;
-        const int t_end = min(T_use, t_begin + ROUTE_TREES_PER_ITEM);
+        const int t_begin = grp * route_tpi<QB>();
+        const int t_end = min(T_use, t_begin + route_tpi<QB>());
         for (int tb = t_begin + warp * G; tb < t_end; tb += nwarps * G) {
             const int t = tb + g;
             const bool tree_ok = t < t_end;
@@ -1845,7 +1846,7 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
                                  &per_sm, &sms);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (ql.m + QB - 1) / QB;
-    const int64_t groups = (ql.n_trees + ROUTE_TREES_PER_ITEM - 1) / ROUTE_TREES_PER_ITEM;
+    const int64_t groups = (ql.n_trees + route_tpi<QB>() - 1) / route_tpi<QB>();
     const int64_t items = tiles * groups;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(items, int64_t(sms) * std::max(per_sm, 1)));
     k_query_route<QB><<<unsigned(blocks), 512, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l,
