@@ -16,7 +16,10 @@
  *     device; the library asks the CUDA runtime which.  Device buffers are
  *     used in place.  Host buffers (pinned or pageable) are staged through
  *     device buffers owned by the index, and a call that was given any host
- *     buffer returns only after its results are in that buffer.
+ *     buffer returns only after its results are in that buffer.  Host
+ *     queries in batches of 8,192 or more are copied in four chunks on a
+ *     second stream owned by the index, each chunk routed as it arrives
+ *     (pinned memory lets the copies overlap the routing).
  *   - A call given only device buffers is stream-ordered on the index's
  *     stream (mrpt_set_stream) and may return before the GPU has finished.
  *     Errors detected on the device (a non-finite query value) are latched
