@@ -532,6 +532,55 @@ def run_build(args):
     return out
 
 
+def run_large(args):
+    """--workload large: queries on the 1M-point configurations.
+    - 1M x 128 heavy-tailed integers (lognormal-int), 10,000 queries, k = 100,
+      T = 100, l = 12; float32 and bfloat16 + float32 re-rank of the top 132;
+    - 1M x 960 rank-64 factors (latent-factor), 1,000 queries, k = 10,
+      T = 200, l = 10; float32, bfloat16 and e4m3 rows with re-rank.
+    v is swept over 1..10.  Each point reports tie-aware recall@k against a
+    float64 brute force and queries/s of device time (L2 flushed before the
+    timed pass)."""
+    import torch
+    import paper_1509_06957_gb300 as mr
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stage = np.zeros(4, np.float32)
+    confs = [("lognormal-int 1000000x128, 10000 queries", workloads.lognormal_int, 128, 10000, 100, 100, 12,
+              [(0, 0), (1, 32)]),
+             ("latent-factor 1000000x960, 1000 queries", workloads.latent_factor, 960, 1000, 10, 200, 10,
+              [(0, 0), (1, 32), (2, 32)])]
+    out = {"metric": "queries/s and tie-aware recall@k on the 1M-point configurations (device time)",
+           "data": "synthetic", "configs": []}
+    for name, gen, d, m, k, T, l, precs in confs:
+        X_np, Q_np = gen(1_000_000, d, m, seed=0)
+        X, Q = torch.from_numpy(X_np).to(dev), torch.from_numpy(Q_np).to(dev)
+        del X_np, Q_np
+        gt_ids, _ = exact_knn_gpu(X, Q, k, torch)
+        kth = torch.cat([((X[gt_ids[s:s + 64, k - 1].long()].double() - Q[s:s + 64].double()) ** 2).sum(1).sqrt()
+                         for s in range(0, m, 64)]).float()[:, None]
+        index = mr.mrpt_build(X, T, l, 0.0, seed=0)
+        mr.mrpt_add_lowp(index, mr.MRPT_PREC_BF16)
+        if any(p == 2 for p, _ in precs):
+            mr.mrpt_add_lowp(index, mr.MRPT_PREC_FP8)
+        rows = []
+        for v in range(1, 11):
+            for prec, margin in precs:
+                mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin)  # warm
+                flush.zero_()
+                _, dists = mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin, stage_ms=stage)
+                rec = float(((dists <= kth * (1 + 1e-5)) & torch.isfinite(dists)).sum()) / (m * k)
+                rows.append(dict(v=v, precision=("fp32", "bf16", "fp8")[prec], margin=margin,
+                                 recall=round(rec, 4), qps=round(m / (float(stage[3]) / 1e3), 1),
+                                 ms=round(float(stage[3]), 3)))
+        index.close()
+        out["configs"].append({"workload": name, "T": T, "depth": l, "k": k, "rows": rows})
+        del X, Q
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return out
+
+
 # ------------------------------------------------------- CPU (oracle) -----
 
 def _oracle_index(X, T, l, seed):
@@ -714,7 +763,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--build-shapes", type=int, default=2, help="build workload: how many shapes")
-    ap.add_argument("--workload", choices=["batch", "stream", "build", "pareto"], default="batch",
+    ap.add_argument("--workload", choices=["batch", "stream", "build", "pareto", "large"], default="batch",
                     help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
     ap.add_argument("--stream-queries", type=int, default=100000)
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp8"], default="auto",
@@ -736,6 +785,8 @@ def main():
         run_build(args)
     elif args.workload == "pareto":
         run_pareto(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_gpu(args)
 
