@@ -1280,6 +1280,173 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
     }
 }
 
+// k_vote_emit for leaves whose share of a chunk is short (large n, small
+// leaves).  Per query (one block, queries taken from an atomic counter):
+//   1. the query's leaf in each tree gives one segment of that tree's leaf
+//      array (ids ascending);
+//   2. per id chunk: clear the 8-bit counters; cut every segment to the ids
+//      of the chunk (a binary search per tree); lay the cut segments end to
+//      end and split that flat list into windows of 128 entries, so windows
+//      stay full however short each tree's share of a chunk is; warps take
+//      contiguous runs of windows;
+//   3. a lane finds the tree of its four entries by a binary search over the
+//      segments' starts, loads the ids and votes them (vote4); the lane whose
+//      increment takes a count from v-1 to v appends the id to the query's
+//      list (Algorithm 4: a point enters S when its count reaches v).  List
+//      order is not fixed; the set is.
+__global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArgs a0) {
+    VoteEmitArgs a = a0;
+    if (a.rec != nullptr) a.m = a.rec->m;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // cnt_words + 32 spare words
+    int32_t *cur = reinterpret_cast<int32_t *>(cnt + a.cnt_words + 32);  // first entry left, per tree
+    int32_t *lend = cur + a.T_use;                                  // end of the query's leaf
+    int32_t *cend = lend + a.T_use;                                 // end inside this chunk
+    int32_t *fpre = cend + a.T_use;                                 // T_use + 1: flat start of each cut segment
+    __shared__ int64_t s_q;
+    __shared__ int s_cnt;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const uint32_t vm1 = uint32_t(a.v - 1);
+    const int T = a.T_use;
+    const uint32_t cnt_s = smem_u32(cnt);
+    const uint32_t spare = 4u * uint32_t(a.cnt_words + lane);
+
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(a.work, 1u);
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi < 0) break;
+        for (int t = tid; t < T; t += VE_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * T + t];
+            cur[t] = a.leaf_off[lf];
+            lend[t] = a.leaf_off[lf + 1];
+        }
+        int32_t *clist = a.cand + qi * int64_t(a.capq);
+        for (int64_t c0 = 0; c0 < a.n; c0 += CH_IDS) {
+            const int64_t wleft = (a.n - c0 + 3) >> 2;
+            const int nwords = int(wleft < a.cnt_words ? wleft : int64_t(a.cnt_words));
+            {
+                uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+                const int n4 = (nwords + 3) >> 2;
+                for (int w = tid; w < n4; w += VE_THREADS) c4[w] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            // this chunk's part of every segment (the thread of tree t also
+            // wrote cur[t] and lend[t])
+            const int64_t lim = c0 + CH_IDS;
+            for (int t = tid; t < T; t += VE_THREADS) {
+                int32_t lo = cur[t], hi = lend[t];
+                const int32_t p = lo;
+                if (lim < a.n) {
+                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (int64_t(__ldg(ids + mid)) < lim)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    hi = lo;
+                }
+                cend[t] = hi;
+                fpre[t] = hi - p;
+            }
+            __syncthreads();
+            if (warp == 0) {  // exclusive scan of the cut lengths
+                int run = 0;
+                for (int b = 0; b < T; b += 32) {
+                    const int t = b + lane;
+                    const int x = t < T ? fpre[t] : 0;
+                    int s = x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, s, o);
+                        if (lane >= o) s += y;
+                    }
+                    if (t < T) fpre[t] = run + s - x;
+                    run += __shfl_sync(0xffffffffu, s, 31);
+                }
+                if (lane == 0) fpre[T] = run;
+            }
+            __syncthreads();
+            const int F = fpre[T];
+            const int W = (F + VE_WIN - 1) / VE_WIN;
+            const int i0 = int((int64_t(W) * warp) / VE_WARPS);
+            const int i1 = int((int64_t(W) * (warp + 1)) / VE_WARPS);
+            const int32_t c0i = int32_t(c0);
+            for (int i = i0; i < i1; ++i) {
+                const int32_t f0 = i * VE_WIN + 4 * lane;  // the lane's first flat entry
+                int32_t e[4] = {0, 0, 0, 0};
+                if (f0 < F) {
+                    int t = 0, hi = T;  // last tree whose cut segment starts at or before f0
+                    while (hi - t > 1) {
+                        const int mid = (t + hi) >> 1;
+                        if (fpre[mid] <= f0)
+                            t = mid;
+                        else
+                            hi = mid;
+                    }
+                    int32_t tn = fpre[t + 1];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t f = f0 + u;
+                        if (f < F) {
+                            while (f >= tn) tn = fpre[++t + 1];
+                            e[u] = __ldg(a.leaf_ids + int64_t(t) * a.n + cur[t] + (f - fpre[t]));
+                        }
+                    }
+                }
+                const uint32_t emask = vote4(cnt_s, make_int4(e[0], e[1], e[2], e[3]), f0, F, c0i,
+                                             spare, vm1);
+                if (emask != 0u) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if ((emask >> u) & 1u) {
+                            const int slot = atomicAdd(&s_cnt, 1);
+                            if (slot < a.capq) clist[slot] = e[u];
+                            if (a.dbg_cand != nullptr && slot < a.cand_cap)
+                                a.dbg_cand[qi * a.cand_cap + slot] = e[u];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            for (int t2 = tid; t2 < T; t2 += VE_THREADS) cur[t2] = cend[t2];
+            if (a.dbg_votes != nullptr) {
+                for (int w = tid; w < nwords; w += VE_THREADS) {
+                    const uint32_t word = cnt[w];
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t id2 = c0 + 4 * int64_t(w) + b;
+                        if (id2 < a.n) a.dbg_votes[qi * a.n + id2] = uint8_t((word >> (8 * b)) & 0xffu);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int c = s_cnt;
+            a.ncand[qi] = c;
+            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
+            if (c > a.capq) {
+                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
+            } else {
+                // work items of the candidate search: chunks of the list (one
+                // even when S is empty, so that the row gets its padding)
+                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
+                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
+                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
+                a.done[qi] = 0;
+            }
+        }
+    }
+}
+
 // k_vote_emit for an index whose ids fit one counter array (n <= 65,536),
 // over the vote layout: every leaf starts on a 16-byte boundary and is padded
 // with the sentinel to a multiple of 4 ids, so a lane's 16-byte load is four
@@ -1951,10 +2118,17 @@ cudaError_t launch_route_any(const mrpt_index *idx, const QueryLaunch &ql, cudaS
 cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
     const int cnt_words = vote_cnt_words(idx->n);
     const bool flat = idx->leaf4 != nullptr;
-    auto kern = flat ? k_vote_flat : k_vote_emit;
-    const size_t smem = flat ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 12
-                             : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
-                                   size_t(4 * ql.n_trees + 1) * 4;
+    // chunked: per-tree windows, or windows over the chunk's segments laid
+    // end to end when a leaf's share of a chunk is short (windows would run
+    // mostly empty)
+    const int64_t leaf_len = (idx->n + idx->L - 1) / idx->L;
+    const int64_t chunks = (idx->n + CH_IDS - 1) / CH_IDS;
+    const bool packed = !flat && leaf_len < 48 * chunks;
+    auto kern = flat ? k_vote_flat : packed ? k_vote_packed : k_vote_emit;
+    const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 12
+                        : packed ? size_t(cnt_words + 32) * 4 + size_t(4 * ql.n_trees + 1) * 4
+                                 : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
+                                       size_t(4 * ql.n_trees + 1) * 4;
     int per_sm = 0, sms = 0;
     cudaError_t e = launch_shape(reinterpret_cast<const void *>(kern), VE_THREADS, smem, idx->device, &per_sm,
                                  &sms);

@@ -113,10 +113,14 @@ def test_vote_threshold_equal_to_T_and_subset_of_trees(mr):
 
 
 @pytest.mark.parametrize("path", PATHS)
-def test_counter_chunks_beyond_shared_memory(mr, path):
-    """n > 65,536 ids: votes are counted in id chunks (per-tree cursors)."""
+@pytest.mark.parametrize("l", [9, 12])
+def test_counter_chunks_beyond_shared_memory(mr, path, l):
+    """n > 65,536 ids: votes are counted in id chunks (per-tree cursors).
+    Depth 9 (leaves of 274, about 91 per chunk) takes per-tree windows;
+    depth 12 (leaves of 35, about 12 per chunk) takes windows over the
+    chunk's segments laid end to end."""
     X, Q = workloads.gaussian_mixture(140000, 8, 12, n_centres=30, seed=10)
-    _full_check(mr, X, Q, 6, 9, 10, 2, 0.5, 4, path=path)
+    _full_check(mr, X, Q, 6, l, 10, 2, 0.5, 4, path=path)
 
 
 def test_degenerate_all_equal_points(mr):
