@@ -772,8 +772,8 @@ def main():
                     help="0: vote/emit + candidate search kernels, 1: one fused kernel")
     ap.add_argument("--T", type=int, default=0, help="fix the number of trees (with --v)")
     ap.add_argument("--v", type=int, default=0, help="fix the vote threshold (with --T)")
-    ap.add_argument("--ref-T", type=int, default=100)
-    ap.add_argument("--ref-v", type=int, default=4)
+    ap.add_argument("--ref-T", type=int, default=100, help="reference arm: trees (the GPU arm's operating point)")
+    ap.add_argument("--ref-v", type=int, default=10, help="reference arm: vote threshold (the GPU arm's operating point)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
