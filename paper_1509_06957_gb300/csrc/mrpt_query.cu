@@ -155,6 +155,202 @@ __global__ void __launch_bounds__(512, 2) k_query_route(
     }
 }
 
+// Routing with two queries per lane, for d small enough that a 64-query
+// tile fits in shared memory dimension-major (xs[dim][64]): one 8-byte load
+// gives a lane both of its queries' components, so every nonzero read feeds
+// 64 fmaf chains.  A unit is (64-query tile, tree); a persistent block of NW
+// warps takes a contiguous unit range, stages each tile once and its warps
+// take the tile's trees in turn.  Each warp streams its tree's nonzero pairs
+// through a two-slot ring in shared memory, CH pairs per slot (one 16-byte
+// cp.async per lane), the next chunk (or the next tree's first) in flight
+// while the current one is read.  The split value of the next level is loaded before the column's
+// chain runs.  Arithmetic per (query, column) is the same fmaf chain in
+// ascending dimension from +0.0f as k_query_route (Algorithm 3).
+constexpr int RP_QT = 64;  // queries per tile (two per lane)
+
+__host__ __device__ constexpr size_t route_pairs_smem(int d, int nw, int ch) {
+    return size_t(d) * RP_QT * sizeof(float) + size_t(nw) * 2 * ch * sizeof(int2);
+}
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int NW, int CH>
+__global__ void __launch_bounds__(NW * 32, 1) k_route_pairs(
+    const float *__restrict__ Q, int64_t m, int32_t d, int32_t T_use, int32_t l, int64_t L,
+    const int2 *__restrict__ rcol, const int2 *__restrict__ dv, const float *__restrict__ split,
+    int32_t *__restrict__ leaf, float *__restrict__ proj, uint32_t *__restrict__ status,
+    const QueryRecord *__restrict__ rec) {
+    static_assert(CH % 2 == 0 && CH <= 64, "a chunk is at most one 16-byte copy per lane");
+    extern __shared__ __align__(16) float xs[];  // d x RP_QT, then NW x 2 x CH pairs
+    if (rec != nullptr) {
+        Q = rec->Q;
+        m = rec->m;
+    }
+    constexpr int NT = NW * 32;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int32_t inner = int32_t(L - 1);
+    const int ncols = T_use * l;
+    const int64_t n_units = ((m + RP_QT - 1) / RP_QT) * int64_t(T_use);
+    const int64_t per = n_units / gridDim.x, extra = n_units % gridDim.x;
+    const int64_t bx = blockIdx.x;
+    int64_t u = bx * per + (bx < extra ? bx : extra);
+    const int64_t u1 = u + per + (bx < extra ? 1 : 0);
+    const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
+    const float2 *xs2 = reinterpret_cast<const float2 *>(xs) + lane;  // this lane's two queries
+    int2 *ring = reinterpret_cast<int2 *>(xs + size_t(d) * RP_QT) + warp * 2 * CH;
+    const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
+
+    // ring state (warp-uniform): slot `cur` holds pairs [cur_lo, cur_lo + CH)
+    // (none at first); the other slot receives nxt_lo (-1: nothing in flight)
+    int cur = 1, cur_lo = -(1 << 30), nxt_lo = -1;
+    // pairs past `hi` (the end of the tree's columns) are zero-filled, never read
+    auto fetch = [&](int slot, int lo, int hi) {
+        const int p = lo + 2 * lane;
+        const bool ok = p + 2 <= hi;
+        if (2 * lane < CH)
+            cp_async16_zfill(ring_s + uint32_t((slot * CH + 2 * lane) * sizeof(int2)), ok ? dv + p : dv,
+                             ok ? 16u : 0u);
+        cp_async_commit();
+    };
+
+    while (u < u1) {
+        const int64_t tile = u / T_use;
+        const int t_a = int(u - tile * T_use);
+        const int64_t t_end = int64_t(t_a) + (u1 - u);
+        const int t_b = t_end < int64_t(T_use) ? int(t_end) : T_use;
+        const int64_t q0 = tile * RP_QT;
+        // ---- stage the tile dimension-major; a query past m reads as zeros
+        __syncthreads();  // the previous tile is no longer read
+        {
+            const int qi = tid & (RP_QT - 1);
+            const int64_t row = q0 + qi;
+            const bool live = row < m;
+            const float *src = Q + (live ? row : 0) * int64_t(d);
+            bool bad = false;
+            if (vec) {
+                for (int c4 = tid / RP_QT; c4 < (d >> 2); c4 += NT / RP_QT) {
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (live) x = __ldg(reinterpret_cast<const float4 *>(src) + c4);
+                    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w));
+                    xs[(4 * c4 + 0) * RP_QT + qi] = x.x;
+                    xs[(4 * c4 + 1) * RP_QT + qi] = x.y;
+                    xs[(4 * c4 + 2) * RP_QT + qi] = x.z;
+                    xs[(4 * c4 + 3) * RP_QT + qi] = x.w;
+                }
+            } else {
+                for (int c = tid / RP_QT; c < d; c += NT / RP_QT) {
+                    const float x = live ? __ldg(src + c) : 0.f;
+                    bad |= !isfinite(x);
+                    xs[c * RP_QT + qi] = x;
+                }
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, STATUS_NONFINITE_QUERY);
+        }
+        __syncthreads();
+        const int64_t qa = q0 + 2 * lane, qb = qa + 1;
+        const bool live_a = qa < m, live_b = qb < m;
+        for (int t = t_a + warp; t < t_b; t += NW) {
+            const int2 *rc = rcol + int64_t(t) * l;
+            const int base = __ldg(&rc[0].x);
+            const int2 last = __ldg(rc + (l - 1));
+            const int hi = last.x + ((last.y + 1) & ~1);  // even end of the tree's pairs
+            const int tn = t + NW;                        // this warp's next tree in the tile
+            const float *sp = split + int64_t(t) * inner;
+            // a chunk fetched for an earlier tree is zero-filled past that
+            // tree's pairs: every tree reads only chunks fetched for it
+            cur_lo = -(1 << 30);
+            int32_t node_a = 0, node_b = 0;
+            for (int j = 0; j < l; ++j) {
+                const int2 sc = __ldg(rc + j);
+                const float s_a = __ldg(sp + node_a), s_b = __ldg(sp + node_b);
+                float acc_a = 0.0f, acc_b = 0.0f;
+                int pos = sc.x;
+                const int cend = sc.x + sc.y;
+                while (pos < cend) {
+                    if (pos < cur_lo || pos >= cur_lo + CH) {
+                        // make the chunk holding `pos` current
+                        const int lo = base + ((pos - base) / CH) * CH;
+                        if (nxt_lo != lo) {
+                            cp_async_wait_all();  // the other slot's copy (if any) is done
+                            __syncwarp();
+                            fetch(cur ^ 1, lo, hi);
+                        }
+                        cp_async_wait_all();
+                        __syncwarp();
+                        cur ^= 1;
+                        cur_lo = lo;
+                        nxt_lo = -1;
+                        // prefetch the next chunk of this tree, else the next tree's first
+                        if (lo + CH < hi) {
+                            nxt_lo = lo + CH;
+                            fetch(cur ^ 1, nxt_lo, hi);
+                        } else if (tn < t_b) {
+                            const int2 *rn = rcol + int64_t(tn) * l;
+                            const int2 nl = __ldg(rn + (l - 1));
+                            const int nb = __ldg(&rn[0].x), nhi = nl.x + ((nl.y + 1) & ~1);
+                            if (nb < nhi) {
+                                nxt_lo = nb;
+                                fetch(cur ^ 1, nb, nhi);
+                            }
+                        }
+                    }
+                    const int lim = min(cend, cur_lo + CH);
+                    const int2 *rs = ring + cur * CH - cur_lo;  // indexed by pair position
+#pragma unroll 2
+                    for (; pos + 4 <= lim; pos += 4) {
+                        const int4 A = *reinterpret_cast<const int4 *>(rs + pos);
+                        const int4 B = *reinterpret_cast<const int4 *>(rs + pos + 2);
+                        const float2 x0 = xs2[A.x * (RP_QT / 2)], x1 = xs2[A.z * (RP_QT / 2)];
+                        const float2 x2 = xs2[B.x * (RP_QT / 2)], x3 = xs2[B.z * (RP_QT / 2)];
+                        acc_a = __fmaf_rn(x0.x, __int_as_float(A.y), acc_a);
+                        acc_b = __fmaf_rn(x0.y, __int_as_float(A.y), acc_b);
+                        acc_a = __fmaf_rn(x1.x, __int_as_float(A.w), acc_a);
+                        acc_b = __fmaf_rn(x1.y, __int_as_float(A.w), acc_b);
+                        acc_a = __fmaf_rn(x2.x, __int_as_float(B.y), acc_a);
+                        acc_b = __fmaf_rn(x2.y, __int_as_float(B.y), acc_b);
+                        acc_a = __fmaf_rn(x3.x, __int_as_float(B.w), acc_a);
+                        acc_b = __fmaf_rn(x3.y, __int_as_float(B.w), acc_b);
+                    }
+                    if (pos + 2 <= lim) {
+                        const int4 A = *reinterpret_cast<const int4 *>(rs + pos);
+                        const float2 x0 = xs2[A.x * (RP_QT / 2)], x1 = xs2[A.z * (RP_QT / 2)];
+                        acc_a = __fmaf_rn(x0.x, __int_as_float(A.y), acc_a);
+                        acc_b = __fmaf_rn(x0.y, __int_as_float(A.y), acc_b);
+                        acc_a = __fmaf_rn(x1.x, __int_as_float(A.w), acc_a);
+                        acc_b = __fmaf_rn(x1.y, __int_as_float(A.w), acc_b);
+                        pos += 2;
+                    }
+                    if (pos < lim) {  // the odd last pair of the column
+                        const int2 P = rs[pos];
+                        const float2 x0 = xs2[P.x * (RP_QT / 2)];
+                        acc_a = __fmaf_rn(x0.x, __int_as_float(P.y), acc_a);
+                        acc_b = __fmaf_rn(x0.y, __int_as_float(P.y), acc_b);
+                        pos += 1;
+                    }
+                }
+                if (proj != nullptr) {
+                    const int c = t * l + j;
+                    if (live_a) proj[qa * ncols + c] = acc_a;
+                    if (live_b) proj[qb * ncols + c] = acc_b;
+                }
+                node_a = 2 * node_a + 1 + (acc_a > s_a ? 1 : 0);
+                node_b = 2 * node_b + 1 + (acc_b > s_b ? 1 : 0);
+            }
+            if (live_a) leaf[qa * T_use + t] = node_a - inner;
+            if (live_b) leaf[qb * T_use + t] = node_b - inner;
+        }
+        u += t_b - t_a;
+    }
+    cp_async_wait_all();  // no copy into shared memory outlives the block
+}
+
 // ---------------------------------------------------------- vote search ----
 
 constexpr int VS_THREADS = 256;
@@ -2023,6 +2219,22 @@ cudaError_t launch_route(const mrpt_index *idx, const QueryLaunch &ql, cudaStrea
     return cudaGetLastError();
 }
 
+// k_route_pairs with NW warps per block and CH pairs per ring slot.
+template <int NW, int CH>
+cudaError_t launch_route_pairs(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    const size_t smem = route_pairs_smem(idx->d, NW, CH);
+    int per_sm = 0, sms = 0;
+    cudaError_t e = launch_shape(reinterpret_cast<const void *>(k_route_pairs<NW, CH>), NW * 32, smem,
+                                 idx->device, &per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    const int64_t units = ((ql.m + RP_QT - 1) / RP_QT) * int64_t(ql.n_trees);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(units, int64_t(sms) * std::max(per_sm, 1)));
+    k_route_pairs<NW, CH><<<unsigned(blocks), NW * 32, smem, s>>>(ql.Q, ql.m, idx->d, ql.n_trees, idx->l,
+                                                                 idx->L, idx->rcol, idx->dv, idx->split,
+                                                                 ql.leaf, ql.proj, idx->status, ql.rec);
+    return cudaGetLastError();
+}
+
 // Shared-memory plan and arguments of k_vote_search.
 template <int KR>
 cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *work,
@@ -2104,8 +2316,18 @@ cudaError_t launch_vote_with_counter(const mrpt_index *idx, const QueryLaunch &q
 
 namespace {
 
+// Largest dynamic shared memory of one block on sm_103 (227 KB).
+constexpr size_t SMEM_BLOCK_MAX = 232448;
+
 cudaError_t launch_route_any(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    // as many queries per block (up to 32, one per lane) as fit in ~110 KB
+    // two queries per lane when a 64-query tile fits (the split descent
+    // needs at least one level): 32 warps per block where their rings fit
+    // beside the tile (d <= 780), else 16 (d <= 844)
+    if (idx->l >= 1) {
+        if (route_pairs_smem(idx->d, 32, 64) <= SMEM_BLOCK_MAX) return launch_route_pairs<32, 64>(idx, ql, s);
+        if (route_pairs_smem(idx->d, 16, 64) <= SMEM_BLOCK_MAX) return launch_route_pairs<16, 64>(idx, ql, s);
+    }
+    // else as many queries per block (up to 32, one per lane) as fit in ~110 KB
     const int64_t per_q = int64_t(idx->d) * 4;
     if (per_q * 32 <= 110 * 1024) return launch_route<32>(idx, ql, s);
     if (per_q * 16 <= 110 * 1024) return launch_route<16>(idx, ql, s);
@@ -2366,20 +2588,7 @@ namespace mrpt {
 int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *work) {
     cudaStream_t s = idx->stream;
     if (ql.m == 0) return MRPT_OK;
-    const int64_t per_q = int64_t(idx->d) * 4;
-    cudaError_t e;
-    if (per_q * 32 <= 110 * 1024)
-        e = launch_route<32>(idx, ql, s);
-    else if (per_q * 16 <= 110 * 1024)
-        e = launch_route<16>(idx, ql, s);
-    else if (per_q * 8 <= 160 * 1024)
-        e = launch_route<8>(idx, ql, s);
-    else if (per_q * 4 <= 160 * 1024)
-        e = launch_route<4>(idx, ql, s);
-    else if (per_q * 2 <= 200 * 1024)
-        e = launch_route<2>(idx, ql, s);
-    else
-        e = launch_route<1>(idx, ql, s);
+    cudaError_t e = launch_route_any(idx, ql, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
     const int kr = (ql.k + 31) / 32;
     if (kr <= 1)

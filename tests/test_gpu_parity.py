@@ -98,6 +98,29 @@ def test_ragged_dimension_and_host_buffers(mr):
     _full_check(mr, X, Q, 7, 4, 10, 2, 0.2, 9, host=True)
 
 
+@pytest.mark.parametrize("d,T,l,density", [
+    (100, 37, 5, 0.1),   # 64-query tiles, 32 warps per block
+    (100, 37, 1, 0.02),  # depth 1; many empty columns
+    (800, 21, 4, 0.05),  # 64-query tiles, 16 warps per block
+    (800, 5, 3, 1.0),    # dense vectors: columns span many ring chunks
+    (900, 19, 4, 0.05),  # tile too large: one query per lane
+])
+def test_routing_kernels(mr, d, T, l, density):
+    """Projections and leaves of every query, bit-exact, for each routing
+    kernel: 150 queries (two full 64-query tiles and a ragged one), tree
+    counts that are not multiples of the warps per block."""
+    X, Q = workloads.gaussian_mixture(3000, d, 150, n_centres=12, seed=d + l)
+    dev = torch.device("cuda:0")
+    idx = mr.mrpt_build(torch.from_numpy(X).to(dev), T, l, density, 21)
+    _, _, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).to(dev), 5, 1, debug=True)
+    torch.cuda.synchronize()
+    ref = oracle.grow_trees(X, T, l, density, 21)
+    _, _, oproj, oleaf, _ = oracle.query(ref, Q, 5, 1, want_internals=True)
+    assert np.array_equal(dbg["proj"].cpu().numpy().view(np.uint32), oproj.view(np.uint32)), "projections"
+    assert np.array_equal(dbg["leaf"].cpu().numpy(), oleaf), "leaf of query"
+    idx.close()
+
+
 def test_single_leaf_is_exact_knn(mr):
     """T = 1, l = 0, v = 1: S = X, so the result is exact k-NN (Sec. I-A)."""
     X, Q = workloads.gaussian_mixture(700, 19, 20, n_centres=4, seed=8)
