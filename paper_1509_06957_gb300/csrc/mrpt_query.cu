@@ -1,9 +1,13 @@
 // Query phase (Sec. III, Algorithms 3-4) on sm_103a.  A batch runs
 //
-//   k_query_route   p = q^T R for every tree and level (Algorithm 3), then
-//                   the descent p[level] <= split -> left.  A block stages
-//                   up to 32 queries in shared memory; one thread per
-//                   (query, tree), lanes of a warp share trees.
+//   k_route_pairs   p = q^T R for every tree and level (Algorithm 3), then
+//                   the descent p[level] <= split -> left, when 64 queries
+//                   fit in shared memory (d <= 844): two queries per lane,
+//                   a warp per tree, nonzeros streamed through a per-warp
+//                   cp.async ring.
+//   k_query_route   the same for larger d: a block stages up to 32 queries;
+//                   one thread per (query, tree), lanes of a warp share
+//                   trees.
 //   k_vote_flat     (n <= 65,536) votes (Algorithm 4's loop) over the
 //                   padded leaf layout: 8-bit counters in shared memory, four
 //                   ids per lane per 16-byte load, one block of PTX per four
@@ -2487,7 +2491,7 @@ cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
 int launch_route_only(mrpt_index *idx, const QueryLaunch &ql) {
     if (ql.m == 0) return MRPT_OK;
     const cudaError_t e = launch_route_any(idx, ql, ql.use_stream ? ql.stream : idx->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    if (e != cudaSuccess) return cuda_fail(e, "routing kernel");
     return MRPT_OK;
 }
 
@@ -2502,7 +2506,7 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
     }
     if (!ql.routed) {
         e = launch_route_any(idx, ql, s);
-        if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+        if (e != cudaSuccess) return cuda_fail(e, "routing kernel");
     }
     if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[1], s));
     const int kr = (ql.k + 31) / 32;
@@ -2589,7 +2593,7 @@ int launch_query_with_counter(mrpt_index *idx, const QueryLaunch &ql, uint32_t *
     cudaStream_t s = idx->stream;
     if (ql.m == 0) return MRPT_OK;
     cudaError_t e = launch_route_any(idx, ql, s);
-    if (e != cudaSuccess) return cuda_fail(e, "k_query_route");
+    if (e != cudaSuccess) return cuda_fail(e, "routing kernel");
     const int kr = (ql.k + 31) / 32;
     if (kr <= 1)
         e = launch_vote_with_counter<1>(idx, ql, s, work);
