@@ -22,6 +22,10 @@ Functions and the passages they follow:
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force, hand-worked fixtures under
 ``tests/golden/`` and invariants stated in Sec. II-III; none is unpinned.
+``tests/test_oracle_mutations.py`` checks that the pins are strong enough: it
+compiles copies of ``mrpt_oracle.c`` with one planted mistake each and runs
+the pins against them through ``MRPT_ORACLE_LIB`` (the path of an oracle
+library to load instead of building this one).
 """
 from __future__ import annotations
 
@@ -65,7 +69,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            lib = ctypes.CDLL(os.environ.get("MRPT_ORACLE_LIB") or build())
             lib.orc_splitmix64.restype = ctypes.c_uint64
             lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_random_matrix.restype = ctypes.c_int64
