@@ -60,7 +60,9 @@ def mnist_like(n: int, m: int, n_prototypes: int = 60, side: int = 28, seed: int
     least 4 px inside the grid), scales the stroke width
     by U(0.8, 1.3) and rasterises: pixels within the stroke core are 255, a
     one-pixel ramp gives intermediate grey values, everything else 0 (about
-    80 % of the pixels; the border stays blank).
+    80 % of the pixels).  The border is almost always blank: a stroke reaches
+    it only when a control point sits at the clamp limit with a wide stroke
+    (about 0.1 % of images).
     """
     g = _rng(seed)
     total = n + m
