@@ -52,3 +52,23 @@ def test_single_rank_aggregate():
     import bench
     total_ms, value = bench.aggregate(200.0, 10000, 5, 1)
     assert total_ms == 200.0 and abs(value - 250000.0) < 1e-9
+
+
+@pytest.mark.slow
+def test_reference_arm_under_torchrun_prints_once():
+    """`bench.py --impl reference` launched as two ranks: rank 0 alone times
+    the oracle and prints one JSON line; the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-3000:]
+    out = lines[0]
+    assert out["impl"] == "reference" and out["value"] > 0 and out["unit"] == "queries/s"
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["e2e"]["h2d_bytes_per_step"] == 0

@@ -94,6 +94,7 @@ def test_pins_pass_on_the_unmodified_oracle(tmp_path):
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
+@pytest.mark.slow
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_planted_mistake(tmp_path, name, old, new):
     src = open(SRC).read()
