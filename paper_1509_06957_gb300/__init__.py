@@ -190,10 +190,43 @@ def _ptr(x):
     if x is None:
         return None
     if _is_torch(x):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous (row-major, tightly packed)")
         return ctypes.c_void_p(x.data_ptr())
-    assert x.flags["C_CONTIGUOUS"]
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous (row-major, tightly packed)")
     return ctypes.c_void_p(x.ctypes.data)
+
+
+_DTYPE_NAMES = {np.float32: "float32", np.int32: "int32"}
+
+
+def _check_matrix(name: str, x, rows: int, cols: int, dtype) -> None:
+    """The C ABI takes a bare pointer and trusts the sizes it is given, so a
+    buffer of another shape or type would be read or written out of bounds:
+    x must be a contiguous rows x cols matrix of `dtype`."""
+    shape = tuple(x.shape)
+    if _is_torch(x):
+        import torch
+        ok_type = x.dtype == {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        contiguous = x.is_contiguous()
+    else:
+        ok_type = np.dtype(x.dtype) == np.dtype(dtype)
+        contiguous = bool(x.flags["C_CONTIGUOUS"])
+    if shape != (rows, cols):
+        raise ValueError(f"{name} must have shape ({rows}, {cols}), got {shape}")
+    if not ok_type:
+        raise ValueError(f"{name} must be {_DTYPE_NAMES[dtype]}, got {x.dtype}")
+    if not contiguous:
+        raise ValueError(f"{name} must be contiguous (row-major, tightly packed)")
+
+
+def _check_queries(Q, index) -> int:
+    """Q must be an m x d matrix for an index of dimension d; returns m."""
+    if len(Q.shape) != 2:
+        raise ValueError(f"queries must be a 2-D (m, d) matrix, got shape {tuple(Q.shape)}")
+    _check_matrix("queries", Q, Q.shape[0], index.d, np.float32)
+    return int(Q.shape[0])
 
 
 def _current_stream(x):
@@ -272,6 +305,8 @@ def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0,
     MRPT_SPARSITY_FIXED (exactly ceil(density * d) per vector)."""
     lib = load_library()
     data = _as_f32(data)
+    if len(data.shape) != 2:
+        raise ValueError(f"data must be a 2-D (n, d) matrix, got shape {tuple(data.shape)}")
     n, d = data.shape
     h = ctypes.c_void_p()
     opts = BuildOpts(int(sparsity))
@@ -337,11 +372,13 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
     (mrpt_add_lowp) and re-ranks the k + ``margin`` nearest in float32."""
     lib = load_library()
     Q = _as_f32(Q)
-    m = Q.shape[0]
+    m = _check_queries(Q, index)
     if out_ids is None:
         out_ids = _empty_like_input(Q, (m, k), np.int32)
     if out_dists is None:
         out_dists = _empty_like_input(Q, (m, k), np.float32)
+    _check_matrix("out_ids", out_ids, m, k, np.int32)
+    _check_matrix("out_dists", out_dists, m, k, np.float32)
     stream = _current_stream(Q)
     if stream is not None:
         _check(lib.mrpt_set_stream(index.handle, stream))
@@ -420,10 +457,13 @@ def mrpt_query_noalloc(index: Index, Q, k: int, v: int, out_ids, out_dists,
     tensors; m * n_trees is limited to MRPT_NOALLOC_MAX_LEAF_ENTRIES; calls
     whose GPU work overlaps share one scratch array and race."""
     lib = load_library()
+    m = _check_queries(Q, index)
+    _check_matrix("out_ids", out_ids, m, k, np.int32)
+    _check_matrix("out_dists", out_dists, m, k, np.float32)
     stream = _current_stream(Q)
     if stream is not None:
         _check(lib.mrpt_set_stream(index.handle, stream))
-    _check(lib.mrpt_query_noalloc(index.handle, _ptr(Q), Q.shape[0], k, v, int(n_trees),
+    _check(lib.mrpt_query_noalloc(index.handle, _ptr(Q), m, k, v, int(n_trees),
                                   _ptr(out_ids), _ptr(out_dists)))
 
 
@@ -445,11 +485,13 @@ class Plan:
 
     def run(self, Q, out_ids=None, out_dists=None):
         Q = _as_f32(Q)
-        m = Q.shape[0]
+        m = _check_queries(Q, self.index)
         if out_ids is None:
             out_ids = _empty_like_input(Q, (m, self.k), np.int32)
         if out_dists is None:
             out_dists = _empty_like_input(Q, (m, self.k), np.float32)
+        _check_matrix("out_ids", out_ids, m, self.k, np.int32)
+        _check_matrix("out_dists", out_dists, m, self.k, np.float32)
         stream = _current_stream(Q)
         if stream is not None:
             _check(self._lib.mrpt_set_stream(self.index.handle, stream))
