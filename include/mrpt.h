@@ -174,7 +174,10 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
 
 /*
  * mrpt_add_lowp -- add a reduced-precision copy of the data to the index for
- * the candidate distances of later queries (mrpt_query_opts.precision).
+ * the candidate distances of later queries (mrpt_query_opts.precision):
+ * the exact search knn(q, k, S) of Algorithm 4 on fewer bytes per row.  The
+ * paper states no precision (Sec. IV-B); this copy has no counterpart there,
+ * and the float32 re-rank restores the exact order of the survivors.
  * MRPT_PREC_BF16: every value rounded to bfloat16 (nearest even), same row
  * layout, 2 bytes per value.  MRPT_PREC_FP8: each row scaled by
  * 448 / max|x| and rounded to e4m3 (saturating), 1 byte per value plus the
@@ -186,7 +189,9 @@ int mrpt_add_lowp(mrpt_index *idx, int32_t precision);
 /*
  * Query plans: the whole query (counter clears and every kernel) captured
  * once into a CUDA graph and replayed per batch, which removes the per-call
- * launch work for streams of small, uneven batches.  A plan fixes k, v and
+ * launch work for streams of small, uneven batches.  They compute exactly
+ * Algorithms 3-4 as mrpt_query does; the paper has no counterpart (it runs
+ * one query at a time on a CPU, Sec. IV).  A plan fixes k, v and
  * the options (n_trees, path, precision, margin, chunk, ring; debug outputs
  * and stage_ms are not available) and a largest batch m_max; it owns its
  * scratch, so plans of one index may run on different streams.  The kernels
@@ -221,21 +226,26 @@ int mrpt_plan_free(mrpt_plan *plan);
 int mrpt_save(const mrpt_index *idx, const char *path);
 int mrpt_load(const char *path, mrpt_index **out);
 
-/* Release the index and everything it owns.  NULL is accepted. */
+/* Release the index and everything it owns.  NULL is accepted.
+ * (Housekeeping: no counterpart in the paper.) */
 int mrpt_free(mrpt_index *idx);
 
-/* Message of the calling thread's last error ("" if none). */
+/* Message of the calling thread's last error ("" if none).
+ * (Housekeeping: no counterpart in the paper.) */
 const char *mrpt_last_error(void);
 
 /* Stream on which the index's work is ordered (a cudaStream_t; NULL is the
- * legacy default stream).  Applies to later calls. */
+ * legacy default stream).  Applies to later calls.
+ * (Housekeeping: no counterpart in the paper.) */
 int mrpt_set_stream(mrpt_index *idx, void *stream);
 
 /* Wait for the index's stream, then report and clear the device-latched
- * status: MRPT_OK or MRPT_ERR_NONFINITE_INPUT / MRPT_ERR_TIMEOUT. */
+ * status: MRPT_OK or MRPT_ERR_NONFINITE_INPUT / MRPT_ERR_TIMEOUT.
+ * (Housekeeping: no counterpart in the paper.) */
 int mrpt_sync(mrpt_index *idx);
 
-/* Shape of an index. */
+/* Shape of an index: n, d (Sec. I-A), T, l, a (Sec. II-B), the seed, the
+ * nonzeros of R and the device memory held. */
 typedef struct mrpt_index_info {
     int64_t n;
     int32_t d, T, l;
@@ -247,7 +257,8 @@ typedef struct mrpt_index_info {
 
 int mrpt_info(const mrpt_index *idx, mrpt_index_info *info);
 
-/* Index contents, for inspection and tests. */
+/* Index contents, for inspection and tests: the random vectors
+ * (Algorithm 1), the split values and leaves (Algorithm 2). */
 enum mrpt_export_what {
     MRPT_EXPORT_R_COL_OFF = 0, /* int32 [T*l+1] column offsets of R (column t*l+j) */
     MRPT_EXPORT_R_DIM = 1,     /* int32 [nnz] dimension of each nonzero, ascending per column */
@@ -258,11 +269,12 @@ enum mrpt_export_what {
     MRPT_EXPORT_DATA = 6       /* float32 [n][d] the index's copy of the data */
 };
 
-/* Bytes that mrpt_export writes for `what` (negative error code if invalid). */
+/* Bytes that mrpt_export writes for `what` (negative error code if invalid);
+ * the parts are those of Algorithms 1-2 listed above. */
 int64_t mrpt_export_size(const mrpt_index *idx, int32_t what);
 
-/* Copy `what` into dst (host or device, dst_bytes >= mrpt_export_size).
- * Synchronous. */
+/* Copy `what` (a part of the index of Algorithms 1-2, listed above) into
+ * dst (host or device, dst_bytes >= mrpt_export_size).  Synchronous. */
 int mrpt_export(const mrpt_index *idx, int32_t what, void *dst, int64_t dst_bytes);
 
 /*
@@ -298,7 +310,7 @@ int mrpt_query_noalloc(mrpt_index *idx, const float *Q, int64_t m, int32_t k, in
 
 /* Fault injection for tests: make the allocation after the next `after`
  * successful ones fail with MRPT_ERR_OOM (negative disables).  Host-side
- * only; process-wide. */
+ * only; process-wide.  (Testing aid: no counterpart in the paper.) */
 int mrpt_debug_fail_alloc_after(int32_t after);
 
 #ifdef __cplusplus

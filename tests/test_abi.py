@@ -86,3 +86,21 @@ def test_oracle_and_library_share_nothing():
     otext = open(os.path.join(ROOT, "oracle", "mrpt_oracle.c")).read()
     assert not any("mrpt.h" in i or "csrc" in i
                    for i in re.findall(r'#include\s+[<"]([^>"]+)', otext))
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration in include/mrpt.h is documented with the passage of
+    the paper it implements (Sec., Algorithm or Table), or says that the
+    paper has no counterpart.  Declarations that follow one another with no
+    comment between them share the comment above the first."""
+    text = open(HEADER).read()
+    cite = re.compile(r"Sec\.|Algorithm|Table|no\s+(?:\*\s+)?counterpart")
+    pos, documented, seen = 0, False, []
+    for m in re.finditer(r"^(?:int|const char|int64_t)\s*\*?\s*(mrpt_\w+)\s*\(", text, flags=re.M):
+        region = text[pos:m.start()]
+        if "/*" in region:
+            documented = bool(cite.search(region))
+        assert documented, f"{m.group(1)}: no citation and no 'no counterpart' in its comment"
+        seen.append(m.group(1))
+        pos = m.end()
+    assert set(seen) == set(declared_functions())
