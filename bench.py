@@ -619,7 +619,7 @@ def cpu_baseline(X, Q, T, v, k, l, target_s=15.0):
     sample = Q[:ns]
     # repeat the sample (bounded) until about target_s of work has been timed
     el, done, reps = 0.0, 0, 0
-    while el < target_s and reps < 64:
+    while el < target_s and reps < 4096:
         t0 = time.perf_counter()
         oracle.query(ref, sample, k, v, mode=1, nthreads=threads)
         el += time.perf_counter() - t0
