@@ -73,6 +73,30 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+HEADLINE_MAX_BYTES = 2048
+# optional keys dropped, in this order, if a headline would not fit
+_DROPPABLE = (("stage_ms",), ("config", "fp32_best"), ("config", "knobs"), ("clocks", "samples"),
+              ("roofline", "peak_kind"), ("cpu_baseline", "single_thread"))
+
+
+def emit_line(out: dict, limit: int = HEADLINE_MAX_BYTES) -> str:
+    """Print `out` as one compact JSON line (the last line of stdout, which
+    the result is read from) and return it.  Optional keys are dropped in a
+    fixed order if the line would be longer than `limit` bytes."""
+    line = json.dumps(out, separators=(",", ":"))
+    for path in _DROPPABLE:
+        if len(line.encode()) <= limit:
+            break
+        node = out
+        for key in path[:-1]:
+            node = node.get(key) if isinstance(node, dict) else None
+        if isinstance(node, dict):
+            node.pop(path[-1], None)
+        line = json.dumps(out, separators=(",", ":"))
+    print(line, flush=True)
+    return line
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -313,9 +337,11 @@ def run_gpu(args):
     L = 1 << l
     leaf_bytes = T_use * math.ceil(n / L) * 4
     # candidate rows in the precision used, plus the float32 rows of the
-    # re-rank (skipped for a lossless bfloat16 copy of this integer data)
+    # re-rank (the library skips it only for a lossless bfloat16 copy)
+    bf16_exact = bool(torch.equal(X, X.bfloat16().float()))
     vbytes = (4, 2, 1)[prec]
-    rerank_rows = 0 if prec == 0 or (prec == 1) else min(k + margin, mean_S)
+    rerank = prec == 2 or (prec == 1 and not bf16_exact)
+    rerank_rows = min(k + margin, mean_S) if rerank else 0
     row_bytes = mean_S * (d * vbytes + (16 if prec == 2 else 0)) + rerank_rows * d * 4
     vote_avg = statistics.mean(vote_ms)
     search_avg = statistics.mean(search_ms)
@@ -333,7 +359,7 @@ def run_gpu(args):
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": load_traffic(name, src),
                 "peak_kind": f"{peak_kind} hbm_gbs", "kernel": name,
-                "algorithmic_bytes_per_query": round(per_query, 1), "avg_ms": round(ms, 4)}
+                "bytes_per_query": round(per_query, 1), "avg_ms": round(ms, 4)}
 
     # ids of at most 65,536 points fit one counter array: the vote kernel
     # then reads the padded leaf layout (k_vote_flat)
@@ -354,27 +380,32 @@ def run_gpu(args):
     # over the step's device time
     path_bytes = leaf_bytes + row_bytes + d * 4 + k * 8
     step_ms = total_ms / args.steps
-    path_roofline = {"bound": "hbm", "achieved": round(path_bytes * m / (step_ms / 1e3) / 1e9, 1),
-                     "peak": peak, "unit": "GB/s",
+    path_roofline = {"achieved": round(path_bytes * m / (step_ms / 1e3) / 1e9, 1),
                      "frac": round(path_bytes * m / (step_ms / 1e3) / 1e9 / peak, 4),
                      "bytes_per_query": round(path_bytes, 1)}
 
     out = None
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline(X_np, Q_np, T_use, v, k, l)
+        detail = {"sweep": sweep, "roofline_other_kernels": others, "tuned_knobs": knobs,
+                  "bf16_exact": bf16_exact}
+        if args.detail_out:
+            with open(args.detail_out, "w") as f:
+                json.dump(detail, f)
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ("f32", "bf16 rows, f32 accumulate (lossless copy: no re-rank)",
+            "dtype": ("f32", "bf16 rows, f32 accumulate" + ("" if rerank else " (lossless copy: no re-rank)"),
                       "e4m3 rows + per-row scale, f32 accumulate + f32 re-rank")[prec],
             "data": "synthetic",
             "config": {"workload": W["name"], "n": n, "d": d, "queries_per_step": m, "k": k,
                        "depth": l, "T": T_use, "v": v, "density": "1/sqrt(d)",
                        "precision": ("fp32", "bf16", "fp8")[prec], "rerank_margin": margin,
-                       "tuned_knobs": knobs,
-                       "fp32_best": best32,
+                       "knobs": {kk: knobs.get(kk) for kk in ("path", "chunk", "ring")},
+                       "fp32_best": None if best32 is None else
+                       {kk: best32[kk] for kk in ("T", "v", "ms", "recall")},
                        "recall_at_10": round(recall_ta, 4),
                        "recall_at_10_strict": round(recall_strict, 4),
                        "mean_candidates": round(mean_S, 1), "build_s_T200": round(build_s, 3),
@@ -384,15 +415,13 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": (2 if args.path == 1 else 4) * args.steps,
             "roofline": roofline,
-            "roofline_other_kernels": others,
             "path_roofline": path_roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "stage_ms": {"route": round(statistics.mean(route_ms), 4),
                          "vote": round(vote_avg, 4), "search": round(search_avg, 4)},
-            "sweep": sweep,
         }
-        print(json.dumps(out), flush=True)
+        emit_line(out)
     index.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -605,19 +634,17 @@ def _oracle_index(X, T, l, seed):
     return oracle.Index(X, T, l, R, P, split, leaf_off, leaf_ids)
 
 
-def cpu_baseline(X, Q, T, v, k, l, target_s=15.0):
-    """The oracle's query path (float32 distances) on all host cores, on a
-    bounded sample of the queries."""
+def _time_oracle(ref, Q, k, v, threads, target_s):
+    """Queries/s of the oracle's query path (float32 distances) with
+    `threads` threads on the first queries of Q, repeated (bounded) until
+    about target_s of work has been timed.  Returns (qps, sample text)."""
     import oracle
-    ref = _oracle_index(X, T, l, WORKLOAD["seed"])
-    threads = oracle.max_threads()
     probe = Q[: max(threads, 8)]
     t0 = time.perf_counter()
     oracle.query(ref, probe, k, v, mode=1, nthreads=threads)
     per_q = (time.perf_counter() - t0) / len(probe)
     ns = int(min(len(Q), max(len(probe), target_s / max(per_q, 1e-6))))
     sample = Q[:ns]
-    # repeat the sample (bounded) until about target_s of work has been timed
     el, done, reps = 0.0, 0, 0
     while el < target_s and reps < 4096:
         t0 = time.perf_counter()
@@ -625,9 +652,20 @@ def cpu_baseline(X, Q, T, v, k, l, target_s=15.0):
         el += time.perf_counter() - t0
         done += ns
         reps += 1
-    return {"value": round(done / el, 2), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {ns} of the {len(Q)} queries x{reps}, T={T}, v={v}, float32 distances, "
-                      f"{el:.1f} s"}
+    return done / el, f"first {ns} of the {len(Q)} queries x{reps}, {el:.1f} s"
+
+
+def cpu_baseline(X, Q, T, v, k, l, target_s=15.0, single_s=5.0):
+    """The oracle's query path (float32 distances) on a bounded sample of
+    the queries: OpenMP over queries on all host cores, and single-threaded."""
+    import oracle
+    ref = _oracle_index(X, T, l, WORKLOAD["seed"])
+    threads = oracle.max_threads()
+    qps, sample = _time_oracle(ref, Q, k, v, threads, target_s)
+    qps1, sample1 = _time_oracle(ref, Q, k, v, 1, single_s)
+    return {"value": round(qps, 2), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sample}, T={T}, v={v}, float32 distances",
+            "single_thread": {"value": round(qps1, 2), "cores": 1, "sample": sample1}}
 
 
 def run_reference(args):
@@ -646,7 +684,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.query(ref, probe, W["k"], v, mode=1, nthreads=threads)
     per_q = (time.perf_counter() - t0) / len(probe)
-    budget = 120.0 / max(1, args.steps + args.warmup)
+    budget = args.ref_budget_s / max(1, args.steps + args.warmup)
     ns = int(min(len(Q), max(threads, budget / max(per_q, 1e-6))))
     for i in range(args.warmup):
         oracle.query(ref, Q[:ns], W["k"], v, mode=1, nthreads=threads)
@@ -669,7 +707,7 @@ def run_reference(args):
                             "sample": f"{ns} queries per step of the {len(Q)}"},
            "e2e": {"value": round(qps, 2), "unit": "queries/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
+    emit_line(out)
     return out
 
 
@@ -774,6 +812,10 @@ def main():
     ap.add_argument("--v", type=int, default=0, help="fix the vote threshold (with --T)")
     ap.add_argument("--ref-T", type=int, default=100, help="reference arm: trees (the GPU arm's operating point)")
     ap.add_argument("--ref-v", type=int, default=10, help="reference arm: vote threshold (the GPU arm's operating point)")
+    ap.add_argument("--ref-budget-s", type=float, default=120.0,
+                    help="reference arm: seconds of oracle work over all warm-up and timed steps")
+    ap.add_argument("--detail-out", default="",
+                    help="write the (T, v, precision) sweep and per-kernel rooflines to this JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -53,3 +53,37 @@ def oracle_sets(ref, leaf, v, T=None):
         _, S = oracle.votes(ref, row, v, T=T)
         out.append(set(S.tolist()))
     return out
+
+
+def check_lowp_results(X, Q, gi, gd, oi, od, cand_sets, min_recall):
+    """Rows from reduced-precision candidate distances with a float32
+    re-rank, against the oracle's exact rows.  The re-rank restores exact
+    order only among the survivors, so a true neighbour may be missing;
+    everything else is exact:
+
+    * padding (-1, +inf) in the oracle's places (min(k, |S|) neighbours);
+    * every returned id is a member of S and unique in its row;
+    * every distance is the exact distance of its id within REL_TOL;
+    * rows ascend by distance;
+    * tie-aware recall against the oracle's k-th distance >= min_recall.
+    Returns that recall."""
+    m, k = oi.shape
+    fin = np.isfinite(od)
+    assert np.array_equal(np.isfinite(gd), fin), "padding differs"
+    assert np.array_equal(gi == -1, ~fin), "padding ids differ"
+    hit = total = 0
+    for i in range(m):
+        got = gi[i][fin[i]]
+        if len(got) == 0:
+            continue
+        assert len(set(got.tolist())) == len(got), f"query {i}: duplicate ids"
+        assert set(got.tolist()) <= cand_sets[i], f"query {i}: id outside S"
+        ex = np.sqrt(((X[got].astype(np.float64) - Q[i].astype(np.float64)) ** 2).sum(1))
+        np.testing.assert_allclose(ex, gd[i][fin[i]], rtol=REL_TOL, atol=1e-30)
+        assert np.all(np.diff(gd[i][fin[i]]) >= 0), f"query {i}: not ascending"
+        kth = od[i][fin[i]][-1]
+        hit += int(np.sum(ex <= kth * (1 + REL_TOL) + 1e-30))
+        total += len(got)
+    rec = hit / max(total, 1)
+    assert rec >= min_recall, f"tie-aware recall {rec:.4f} below {min_recall}"
+    return rec

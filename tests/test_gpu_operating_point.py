@@ -1,0 +1,134 @@
+"""GPU parity at the operating point that bench.py times, against the oracle.
+
+The benchmark answers 10,000 queries against the 60,000 x 784 mnist-like
+index (depth 8) with the first T = 100 of 200 trees, v = 10, k = 10.  With
+that many queries every persistent vote block takes many queries in turn
+(its counter clear, its claim of the next query and the look-up of that
+query's leaves while the current one votes), which small batches never
+exercise.  Here the whole batch runs in the launch configurations the bench
+uses -- float32 rows, bfloat16 rows with the tuned work-item size and ring
+(chunk 32, ring 2), e4m3 rows with re-rank, and the fused one-kernel path --
+and every row is compared with the oracle (Algorithms 3-4).  A debug pass over
+2,400 queries compares the leaf of every query, |S| of every query, and the
+vote counts F(x;q) and candidate set S of 240 queries spread over the batch.
+
+The same is done for ids beyond one shared-memory counter array
+(n = 140,000: the chunked vote kernels) with 2,000 queries."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import check_lowp_results, check_results, oracle_sets
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N, D, M, L, T_MAX, T, V, K = 60000, 784, 10000, 8, 200, 100, 10, 10
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1509_06957_gb300 as m
+    m.load_library()
+    return m
+
+
+@pytest.fixture(scope="module")
+def bench_case(mr):
+    X, Q = workloads.mnist_like(N, M, seed=0)
+    dev = torch.device("cuda:0")
+    idx = mr.mrpt_build(torch.from_numpy(X).to(dev), T_MAX, L, 0.0, seed=0)
+    mr.mrpt_add_lowp(idx, mr.MRPT_PREC_BF16)
+    mr.mrpt_add_lowp(idx, mr.MRPT_PREC_FP8)
+    dens = float(np.float32(1.0 / np.sqrt(D)))
+    ref = oracle.grow_trees(X, T, L, dens, 0)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, K, V, want_internals=True)
+    yield dict(X=X, Q=Q, Qd=torch.from_numpy(Q).to(dev), idx=idx, ref=ref, oi=oi, od=od,
+               oleaf=oleaf, oncand=oncand)
+    idx.close()
+
+
+def test_first_trees_equal_the_oracles(mr, bench_case):
+    """The index's first 100 trees (prefix-stable) are the oracle's."""
+    c = bench_case
+    ref = c["ref"]
+    assert np.array_equal(mr.mrpt_export(c["idx"], "SPLIT")[:T].view(np.uint32),
+                          ref.split.view(np.uint32))
+    assert np.array_equal(mr.mrpt_export(c["idx"], "LEAF_IDS")[:T], ref.leaf_ids)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(),                                    # float32 rows, default knobs
+    dict(precision=1, margin=0, chunk=32, ring=2),  # bfloat16 rows, the tuned knobs
+    dict(precision=1, margin=8, chunk=32, ring=2),
+    dict(precision=2, margin=8),               # e4m3 rows + float32 re-rank
+    dict(path=1),                              # one fused kernel
+], ids=["fp32", "bf16-tuned", "bf16-margin8", "fp8", "fused"])
+def test_every_row_at_the_operating_point(mr, bench_case, opts):
+    c = bench_case
+    ids, dists = mr.mrpt_query_ex(c["idx"], c["Qd"], K, V, n_trees=T, **opts)
+    torch.cuda.synchronize()
+    gi, gd = ids.cpu().numpy(), dists.cpu().numpy()
+    if opts.get("precision") == 2:
+        # e4m3 rows are lossy: the re-rank is exact only among the survivors
+        check_lowp_results(c["X"], c["Q"], gi, gd, c["oi"], c["od"],
+                           oracle_sets(c["ref"], c["oleaf"], V), min_recall=0.97)
+        return
+    diff = np.nonzero((gi != c["oi"]).any(1))[0]
+    sets = {int(i): s for i, s in zip(diff, oracle_sets(c["ref"], c["oleaf"][diff], V))}
+    check_results(c["X"], c["Q"], gi, gd, c["oi"], c["od"],
+                  cand_sets=[sets.get(i) or set() for i in range(M)])
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_internals_over_a_large_batch(mr, bench_case, path):
+    c = bench_case
+    m = 2400
+    ids, dists, dbg = mr.mrpt_query_ex(c["idx"], c["Qd"][:m], K, V, n_trees=T, debug=True,
+                                       cand_cap=512, path=path)
+    torch.cuda.synchronize()
+    leaf = dbg["leaf"].cpu().numpy()
+    ncand = dbg["n_cand"].cpu().numpy()
+    assert np.array_equal(leaf, c["oleaf"][:m]), "leaf of query"
+    assert np.array_equal(ncand, c["oncand"][:m]), "|S|"
+    assert ncand.max() <= 512
+    cand = dbg["cand"].cpu().numpy()
+    sample = np.arange(0, m, 10)
+    votes = dbg["votes"][torch.from_numpy(sample).cuda()].cpu().numpy()
+    for j, i in enumerate(sample):
+        F, S = oracle.votes(c["ref"], c["oleaf"][i], V)
+        assert np.array_equal(votes[j], F.astype(np.uint8)), f"votes of query {i}"
+        assert set(cand[i][: ncand[i]].tolist()) == set(S.tolist()), f"candidate set of query {i}"
+    check_results(c["X"], c["Q"][:m], ids.cpu().numpy(), dists.cpu().numpy(), c["oi"][:m],
+                  c["od"][:m], oracle_sets(c["ref"], c["oleaf"][:m], V))
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("l", [9, 12])
+def test_chunked_votes_over_a_large_batch(mr, l, path):
+    """n = 140,000 (counters in three id chunks): depth 9 takes per-tree
+    windows (k_vote_emit), depth 12 the packed segments (k_vote_packed)."""
+    n, d, m, T_, v, k = 140000, 8, 2000, 20, 3, 10
+    X, Q = workloads.gaussian_mixture(n, d, m, n_centres=30, seed=14)
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T_, l, 0.5, 4)
+    ids, dists, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, debug=True,
+                                       cand_cap=2048, path=path)
+    torch.cuda.synchronize()
+    ref = oracle.grow_trees(X, T_, l, 0.5, 4)
+    assert np.array_equal(mr.mrpt_export(idx, "LEAF_IDS"), ref.leaf_ids)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, k, v, want_internals=True)
+    assert np.array_equal(dbg["leaf"].cpu().numpy(), oleaf), "leaf of query"
+    ncand = dbg["n_cand"].cpu().numpy()
+    assert np.array_equal(ncand, oncand), "|S|"
+    cand = dbg["cand"].cpu().numpy()
+    sample = np.arange(0, m, 10)
+    votes = dbg["votes"][torch.from_numpy(sample).cuda()].cpu().numpy()
+    for j, i in enumerate(sample):
+        F, S = oracle.votes(ref, oleaf[i], v)
+        assert np.array_equal(votes[j], F.astype(np.uint8)), f"votes of query {i}"
+        assert set(cand[i][: ncand[i]].tolist()) == set(S.tolist()), f"candidate set of query {i}"
+    check_results(X, Q, ids.cpu().numpy(), dists.cpu().numpy(), oi, od, oracle_sets(ref, oleaf, v))
+    idx.close()

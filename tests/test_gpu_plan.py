@@ -1,11 +1,13 @@
 """GPU: query plans (the whole query captured in a CUDA graph, replayed per
-batch with the batch read from a device record) give the same rows as
-mrpt_query_ex, for any batch size up to the plan's maximum."""
+batch with the batch read from a device record) give the oracle's rows
+(Algorithms 3-4), for any batch size up to the plan's maximum, in every
+option set a plan can fix."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads
-from _parity import REL_TOL
+from _parity import check_results, oracle_sets
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -25,43 +27,42 @@ def setup(mr):
     X, Q = workloads.mnist_like(8000, 600, seed=9)
     idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 24, 6, 0.0, 3)
     mr.mrpt_add_lowp(idx)
-    yield idx, torch.from_numpy(Q).cuda()
+    ref = oracle.grow_trees(X, 24, 6, float(np.float32(1 / np.sqrt(784))), 3)
+    yield idx, X, Q, torch.from_numpy(Q).cuda(), ref
     idx.close()
 
 
-def _same(a_ids, a_d, b_ids, b_d):
-    a_ids, a_d, b_ids, b_d = (t.cpu().numpy() if hasattr(t, "cpu") else t for t in (a_ids, a_d, b_ids, b_d))
-    fin = np.isfinite(b_d)
-    assert np.array_equal(np.isfinite(a_d), fin)
-    np.testing.assert_allclose(a_d[fin], b_d[fin], rtol=REL_TOL)
-    diff = (a_ids != b_ids) & fin
-    if diff.any():  # only between equal distances
-        np.testing.assert_allclose(a_d[diff], b_d[diff], rtol=REL_TOL)
+def _oracle_rows(ref, Q, k, v, T):
+    oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, T=T, want_internals=True)
+    return oi, od, oracle_sets(ref, oleaf, v, T=T)
+
+
+def _np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else t
 
 
 @pytest.mark.parametrize("opts", [dict(), dict(path=1), dict(precision=1, margin=8),
                                   dict(n_trees=12, chunk=64, ring=3)])
-def test_plan_matches_query_for_any_batch(mr, setup, opts):
-    idx, Q = setup
+def test_plan_matches_the_oracle_for_any_batch(mr, setup, opts):
+    idx, X, Q, Qd, ref = setup
     k, v = 10, 3
+    oi, od, sets = _oracle_rows(ref, Q, k, v, opts.get("n_trees") or 24)
     plan = mr.Plan(idx, 512, k, v, **opts)
     for m in (1, 37, 256, 512, 5):
-        ids, d = plan.run(Q[:m])
-        rids, rd = mr.mrpt_query_ex(idx, Q[:m], k, v, **opts)
+        ids, d = plan.run(Qd[:m])
         torch.cuda.synchronize()
-        _same(ids, d, rids, rd)
+        check_results(X, Q[:m], _np(ids), _np(d), oi[:m], od[:m], sets[:m])
     plan.close()
 
 
 def test_plan_host_buffers_and_limits(mr, setup):
-    idx, Q = setup
+    idx, X, Q, Qd, ref = setup
+    oi, od, sets = _oracle_rows(ref, Q[:50], 5, 2, 24)
     plan = mr.Plan(idx, 64, 5, 2)
-    qh = Q[:50].cpu().numpy()
-    ids, d = plan.run(qh)
-    rids, rd = mr.mrpt_query_ex(idx, qh, 5, 2)
-    _same(ids, d, rids, rd)
+    ids, d = plan.run(Q[:50].copy())
+    check_results(X, Q[:50], _np(ids), _np(d), oi, od, sets)
     with pytest.raises(mr.MRPTError) as e:
-        plan.run(Q[:65])
+        plan.run(Qd[:65])
     assert e.value.code == mr.MRPT_ERR_INVALID_ARG
     plan.close()
     with pytest.raises(mr.MRPTError):

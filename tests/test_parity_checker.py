@@ -94,3 +94,57 @@ def test_swap_at_an_exact_tie_passes(case):
                 check_results(X, Q, gi, dists.copy(), ids, dists, sets)
                 return
     pytest.skip("no exact tie in this sample")
+
+
+# ---- the reduced-precision comparison (ids in S, exact distances, recall)
+
+def test_lowp_oracle_answer_passes(case):
+    from _parity import check_lowp_results
+    X, Q, ids, dists, sets = case
+    assert check_lowp_results(X, Q, ids.copy(), dists.copy(), ids, dists, sets, 1.0) == 1.0
+
+
+def test_lowp_missing_neighbour_lowers_recall(case):
+    """A true neighbour replaced by the next member of S (its exact
+    distance reported, the row re-sorted) passes the exactness checks and
+    lowers the recall: the bound decides."""
+    from _parity import check_lowp_results
+    X, Q, ids, dists, sets = case
+    i = _row_with_full_result(dists)
+    S = np.array(sorted(sets[i]))
+    ex = np.sqrt(((X[S].astype(np.float64) - Q[i].astype(np.float64)) ** 2).sum(1))
+    order = np.lexsort((S, ex))
+    k = ids.shape[1]
+    if len(S) <= k:
+        pytest.skip("S too small")
+    pick = np.concatenate([order[1:k], order[k:k + 1]])      # drop the nearest, take the (k+1)-th
+    if ex[order[k]] <= dists[i, -1] * (1 + REL_TOL):
+        pytest.skip("the (k+1)-th ties the k-th")
+    gi, gd = ids.copy(), dists.copy()
+    gi[i], gd[i] = S[pick], ex[pick].astype(np.float32)
+    rec = check_lowp_results(X, Q, gi, gd, ids, dists, sets, 0.0)
+    assert rec < 1.0
+    with pytest.raises(AssertionError):
+        check_lowp_results(X, Q, gi, gd, ids, dists, sets, 1.0)
+
+
+@pytest.mark.parametrize("mistake", ["outside", "distance", "order", "duplicate", "padding"])
+def test_lowp_planted_errors_fail(case, mistake):
+    from _parity import check_lowp_results
+    X, Q, ids, dists, sets = case
+    i = _row_with_full_result(dists)
+    gi, gd = ids.copy(), dists.copy()
+    if mistake == "outside":
+        gi[i, 0] = next(x for x in range(len(X)) if x not in sets[i])
+    elif mistake == "distance":
+        gd[i, 3] *= 1 + 10 * REL_TOL
+    elif mistake == "order":
+        gi[i, [2, 7]], gd[i, [2, 7]] = gi[i, [7, 2]], gd[i, [7, 2]]
+        if gd[i, 2] == gd[i, 7]:
+            pytest.skip("tie")
+    elif mistake == "duplicate":
+        gi[i, 1], gd[i, 1] = gi[i, 0], gd[i, 0]
+    else:
+        gi[i, -1], gd[i, -1] = -1, np.inf
+    with pytest.raises(AssertionError):
+        check_lowp_results(X, Q, gi, gd, ids, dists, sets, 0.0)

@@ -1,17 +1,20 @@
 """mrpt_query_noalloc: the query for callers that may not allocate device
 memory (a serving loop with a latency budget, where cudaMalloc/cudaFree can
 synchronise the device, or a process whose device memory belongs to another
-framework's pool).  It must give what mrpt_query gives, on consecutive
-calls that reuse its one fixed scratch array, and refuse batches larger
-than that array.  Collected last on purpose (file name), so that a run
-stopping at the first failure has already run every other test."""
+framework's pool).  On consecutive calls that reuse its one fixed scratch
+array it must give the oracle's rows (Algorithms 3-4) -- the rows mrpt_query
+gives -- while every device allocation of the library is made to fail, and it
+must refuse batches larger than that array.  Collected last on purpose (file
+name), so that a run stopping at the first failure has already run every
+other test."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
-from _parity import REL_TOL
+from _parity import check_results, oracle_sets
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,24 +42,31 @@ def _noalloc(mr, idx, Q, k, v, n_trees=0):
     return rc, ids.cpu().numpy(), dists.cpu().numpy()
 
 
-def test_noalloc_matches_mrpt_query_on_consecutive_calls(mr):
+def test_noalloc_matches_the_oracle_on_consecutive_calls(mr):
     X, Q = workloads.mnist_like(5000, 300, seed=5)
     dev = torch.device("cuda:0")
+    # a fresh index: none of its query scratch has been allocated yet
     idx = mr.mrpt_build(torch.from_numpy(X).to(dev), 24, 5, 0.0, seed=2)
+    ref = oracle.grow_trees(X, 24, 5, float(np.float32(1 / np.sqrt(784))), 2)
     Qd = torch.from_numpy(Q).to(dev)
     for k, v, n_trees in [(10, 3, 0), (100, 2, 16)]:
-        ref_ids, ref_d = mr.mrpt_query(idx, Qd, k, v, n_trees=n_trees)
-        ref_ids, ref_d = ref_ids.cpu().numpy(), ref_d.cpu().numpy()
+        oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, T=n_trees or 24, want_internals=True)
+        sets = oracle_sets(ref, oleaf, v, T=n_trees or 24)
         for call in range(2):
-            rc, ids, dists = _noalloc(mr, idx, Qd, k, v, n_trees)
+            # the next device allocation of the library fails: the calls
+            # below succeed only because they make none
+            mr.mrpt_debug_fail_alloc_after(0)
+            try:
+                rc, ids, dists = _noalloc(mr, idx, Qd, k, v, n_trees)
+            finally:
+                mr.mrpt_debug_fail_alloc_after(-1)
             assert rc == 0, mr.mrpt_last_error()
-            fin = np.isfinite(ref_d)
-            assert np.array_equal(np.isfinite(dists), fin)
-            np.testing.assert_allclose(dists[fin], ref_d[fin], rtol=REL_TOL, atol=1e-30)
-            same = (ids == ref_ids) | ~fin
-            # ids may differ only between equal distances
-            if not same.all():
-                np.testing.assert_allclose(dists[~same], ref_d[~same], rtol=REL_TOL)
+            check_results(X, Q, ids, dists, oi, od, sets)
+        # the allocating entry point gives the same rows
+        ref_ids, ref_d = mr.mrpt_query(idx, Qd, k, v, n_trees=n_trees)
+        check_results(X, Q, ref_ids.cpu().numpy(), ref_d.cpu().numpy(), oi, od, sets)
+    # allocation works again afterwards
+    mr.mrpt_query(idx, Qd[:4], 5, 1)
     idx.close()
 
 
