@@ -413,7 +413,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}",
                        "path": "fused" if args.path == 1 else "vote-emit + candidate-search"},
             "e2e": e2e,
-            "gpu_launches": (2 if args.path == 1 else 4) * args.steps,
+            "gpu_launches": (2 if args.path == 1 else 3) * args.steps,
             "roofline": roofline,
             "path_roofline": path_roofline,
             "cpu_baseline": cpu,

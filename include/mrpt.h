@@ -124,6 +124,11 @@ int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l,
  *              (distance, id) ascending; -1 where |S| < k.
  *   out_dists  m x k float32 Euclidean distances (Sec. I-A), +inf where
  *              |S| < k.  Distances are accumulated in float32.
+ * The default path keeps each query's S in a device list of
+ * T ceil(n/2^l) / v entries (at most n), the most S can hold (Sec. III-B), and
+ * splits the exact search on S into chunks that warps take in turn; when the
+ * lists of the whole batch would take more than 2 GiB the batch runs as
+ * consecutive sub-batches.  The scratch stays with the index for later calls.
  * Equivalent to mrpt_query_ex with opts = NULL.
  * Errors: INVALID_ARG, NONFINITE_INPUT (latched, see above), OOM, CUDA.
  */
@@ -143,9 +148,7 @@ typedef struct mrpt_query_opts {
                              re-ranked with exact float32 distances.  When the bfloat16
                              copy is lossless (every value exactly a bfloat16) those
                              distances are the float32 ones up to summation order and
-                             the re-rank is skipped.  Path 0 only; a query whose
-                             candidate list overflows is answered in float32
-                             throughout. */
+                             the re-rank is skipped.  Path 0 only. */
     int32_t margin;       /* survivors beyond k kept for the re-rank (k + margin <= 256) */
     int32_t chunk;        /* tuning, path 0: candidates per search work item (0 = auto) */
     int32_t ring;         /* tuning, path 0: candidate rows staged per search warp, 2..16
@@ -312,6 +315,17 @@ int mrpt_query_noalloc(mrpt_index *idx, const float *Q, int64_t m, int32_t k, in
  * successful ones fail with MRPT_ERR_OOM (negative disables).  Host-side
  * only; process-wide.  (Testing aid: no counterpart in the paper.) */
 int mrpt_debug_fail_alloc_after(int32_t after);
+
+/* Fault injection for tests: each wait for a staged candidate row in the
+ * candidate search's distance loop (path 0) gives up after `tries` tries
+ * instead of about two million (negative restores the full bound).  A warp
+ * whose wait gives up stops, sets the index's status to MRPT_ERR_TIMEOUT
+ * (reported by mrpt_sync, or by a call given host buffers) and first waits,
+ * with the full bound, for its row copies still in flight; the rows of the
+ * queries it held are not written.  Applies to launches made after the
+ * call, including plans created after it.  Process-wide; host-side
+ * setting only.  (Testing aid: no counterpart in the paper.) */
+int mrpt_debug_row_wait_tries(int32_t tries);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,7 @@ ABI_SYMBOLS = (
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
     "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
     "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free", "mrpt_save", "mrpt_load",
-    "mrpt_build_ex",
+    "mrpt_build_ex", "mrpt_debug_row_wait_tries",
 )
 MRPT_SPARSITY_BERNOULLI = 0
 MRPT_SPARSITY_FIXED = 1
@@ -151,6 +151,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_export.argtypes = [vp, i32, vp, i64]
         lib.mrpt_debug_fail_alloc_after.restype = ctypes.c_int
         lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
+        lib.mrpt_debug_row_wait_tries.restype = ctypes.c_int
+        lib.mrpt_debug_row_wait_tries.argtypes = [i32]
         lib.mrpt_plan_create.restype = ctypes.c_int
         lib.mrpt_plan_create.argtypes = [vp, i64, i32, i32, ctypes.POINTER(QueryOpts),
                                          ctypes.POINTER(vp)]
@@ -447,6 +449,12 @@ def mrpt_export(index: Index, what: str) -> np.ndarray:
 
 def mrpt_debug_fail_alloc_after(after: int) -> None:
     _check(load_library().mrpt_debug_fail_alloc_after(int(after)))
+
+
+def mrpt_debug_row_wait_tries(tries: int) -> None:
+    """Testing aid: shorten the candidate search's row waits to `tries`
+    tries (negative restores the full bound); see mrpt.h."""
+    _check(load_library().mrpt_debug_row_wait_tries(int(tries)))
 
 
 def mrpt_query_noalloc(index: Index, Q, k: int, v: int, out_ids, out_dists,

@@ -17,11 +17,18 @@ namespace mrpt {
 
 namespace {
 thread_local std::string g_last_error;
-// Longest candidate list per query kept for the two-kernel query path;
-// queries with more candidates are answered by the fused kernel.
-constexpr int64_t kCandListCap = 2048;
+// Scratch of the two-kernel path (candidate lists, work items, partial
+// lists) that one launch may use; a batch that needs more runs in
+// consecutive sub-batches.
+constexpr size_t kCandScratchBudget = size_t(2) << 30;
 std::atomic<int32_t> g_fail_after{-1};
+std::atomic<int32_t> g_row_wait_tries{-1};
 }  // namespace
+
+uint32_t debug_row_wait_tries() {
+    const int32_t t = g_row_wait_tries.load();
+    return t < 0 ? (1u << 21) : uint32_t(t);
+}
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
@@ -147,8 +154,8 @@ static void free_index(mrpt_index *idx) {
 }
 
 // Scratch of the two-kernel query path for m queries: candidate lists,
-// work items, per-chunk partial top-k lists, |S|, overflow list and
-// per-query completion counters, each starting on a 256-byte boundary.
+// work items, per-chunk partial top-k lists, |S| and per-query completion
+// counters, each starting on a 256-byte boundary.
 struct CandLayout {
     int32_t capq, chunk, max_items_q, ring;
     size_t lb, ib, pb, nb, total;
@@ -160,24 +167,25 @@ static CandLayout cand_layout(const mrpt_index *idx, int64_t m, int32_t k, int32
     CandLayout L{};
     const int64_t ks = int64_t(k) + margin;  // list length kept per chunk
     // |S| <= T ceil(n / 2^l) / v (Sec. III-B: every member of S holds at
-    // least v of the T ceil(n / 2^l) votes), and |S| <= n
+    // least v of the T ceil(n / 2^l) votes), and |S| <= n: a list of that
+    // length holds every candidate of any query
     const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
     int64_t bound = int64_t(n_trees) * leaf_max / v;
     if (bound > idx->n) bound = idx->n;
-    L.capq = int32_t(bound < kCandListCap ? bound : kCandListCap);
-    if (L.capq < 1) L.capq = 1;
+    L.capq = int32_t(bound < 1 ? 1 : bound);
     // candidate-search work items: chunks of a list, at least 2(k + margin)
-    // candidates and 64 (float32) or 32 (bfloat16) each
+    // candidates and 64 (float32) or 32 (bfloat16) each, at most
+    // CAND_ITEMS_MAX per query
     L.chunk = int32_t(std::max<int64_t>(precision != MRPT_PREC_FP32 ? 32 : 64, ((2 * ks + 31) / 32) * 32));
     if (opts && opts->chunk > 0) L.chunk = int32_t(std::max<int64_t>(opts->chunk, ks));
     L.ring = (opts && opts->ring > 0) ? std::min<int32_t>(std::max<int32_t>(opts->ring, 2), 16) : 0;
-    L.max_items_q = (L.capq + L.chunk - 1) / L.chunk;
+    L.max_items_q = int32_t(std::min<int64_t>((int64_t(L.capq) + L.chunk - 1) / L.chunk, CAND_ITEMS_MAX));
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     L.lb = up(size_t(m) * size_t(L.capq) * 4);
     L.ib = up(size_t(m) * size_t(L.max_items_q) * 8);
     L.pb = up(size_t(m) * size_t(L.max_items_q) * size_t(ks) * 4);
     L.nb = up(size_t(m) * 4);
-    L.total = L.lb + L.ib + 2 * L.pb + 3 * L.nb;
+    L.total = L.lb + L.ib + 2 * L.pb + 2 * L.nb;
     return L;
 }
 
@@ -192,8 +200,7 @@ static void cand_carve(const CandLayout &L, char *base, int64_t m, QueryLaunch &
     ql.part_d = reinterpret_cast<float *>(base + L.lb + L.ib);
     ql.part_i = reinterpret_cast<int32_t *>(base + L.lb + L.ib + L.pb);
     ql.ncand = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb);
-    ql.overflow = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb + L.nb);
-    ql.done = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb + 2 * L.nb);
+    ql.done = reinterpret_cast<int32_t *>(base + L.lb + L.ib + 2 * L.pb + L.nb);
 }
 
 }  // namespace mrpt
@@ -221,6 +228,11 @@ const char *mrpt_last_error(void) { return g_last_error.c_str(); }
 
 int mrpt_debug_fail_alloc_after(int32_t after) {
     g_fail_after.store(after < 0 ? -1 : after);
+    return MRPT_OK;
+}
+
+int mrpt_debug_row_wait_tries(int32_t tries) {
+    g_row_wait_tries.store(tries < 0 ? -1 : tries);
     return MRPT_OK;
 }
 
@@ -518,10 +530,18 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
     ql.path = opts ? opts->path : 0;
     ql.precision = precision;
     ql.margin = margin;
+    // two-kernel path: candidate lists for mb queries at a time, mb = m
+    // unless their scratch would pass kCandScratchBudget
+    int64_t mb = m;
     if (ql.path == 0) {
-        const CandLayout lay = cand_layout(idx, m, k, v, n_trees, precision, margin, opts);
+        CandLayout lay = cand_layout(idx, m, k, v, n_trees, precision, margin, opts);
+        if (lay.total > kCandScratchBudget) {
+            const CandLayout one = cand_layout(idx, 1, k, v, n_trees, precision, margin, opts);
+            mb = std::max<int64_t>(1, int64_t(kCandScratchBudget / one.total));
+            lay = cand_layout(idx, mb, k, v, n_trees, precision, margin, opts);
+        }
         if ((rc = idx->q_cand.ensure(lay.total, "candidate lists"))) return rc;
-        cand_carve(lay, static_cast<char *>(idx->q_cand.ptr), m, ql);
+        cand_carve(lay, static_cast<char *>(idx->q_cand.ptr), mb, ql);
     }
 
     if (chunked_in) {
@@ -551,7 +571,30 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
         }
         ql.routed = true;
     }
-    if ((rc = launch_query(idx, ql))) return rc;
+    if (mb >= m) {
+        if ((rc = launch_query(idx, ql))) return rc;
+    } else {
+        // consecutive sub-batches reuse the candidate scratch; stage times add up
+        float acc[4] = {0.f, 0.f, 0.f, 0.f}, part[4];
+        for (int64_t q0 = 0; q0 < m; q0 += mb) {
+            QueryLaunch qb = ql;
+            qb.m = std::min(mb, m - q0);
+            qb.Q = ql.Q + q0 * idx->d;
+            qb.out_ids = ql.out_ids + q0 * k;
+            qb.out_dists = ql.out_dists + q0 * k;
+            qb.leaf = ql.leaf + q0 * n_trees;
+            if (ql.proj) qb.proj = ql.proj + q0 * int64_t(n_trees) * idx->l;
+            if (ql.votes) qb.votes = ql.votes + q0 * idx->n;
+            if (ql.n_cand) qb.n_cand = ql.n_cand + q0;
+            if (ql.cand) qb.cand = ql.cand + q0 * ql.cand_cap;
+            qb.stage_ms = ql.stage_ms ? part : nullptr;
+            if ((rc = launch_query(idx, qb))) return rc;
+            if (ql.stage_ms)
+                for (int i = 0; i < 4; ++i) acc[i] += part[i];
+        }
+        if (ql.stage_ms)
+            for (int i = 0; i < 4; ++i) ql.stage_ms[i] = acc[i];
+    }
 
     // ---- copy staged results back
     if (!ids_dev) MRPT_CUDA_TRY(cudaMemcpyAsync(out_ids, ids_d, ob, cudaMemcpyDeviceToHost, s));

@@ -25,6 +25,10 @@ int cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::mrpt::cuda_fail(_e, #call);  \
     } while (0)
 
+// Tries of each row wait in the candidate search's distance loop: the full
+// bound unless a test has shortened it (mrpt_debug_row_wait_tries).
+uint32_t debug_row_wait_tries();
+
 // Device allocation through one gate so that tests can inject failures.
 int dev_alloc(void **p, size_t bytes, const char *what);
 
@@ -91,7 +95,7 @@ struct mrpt_index {
     mrpt::Scratch q_stage;   // staged host queries (m x d)
     mrpt::Scratch o_stage;   // staged outputs (m x k ids + m x k dists)
     mrpt::Scratch dbg_stage; // staged debug outputs
-    mrpt::Scratch q_cand;    // candidate lists, |S| per query, overflow list
+    mrpt::Scratch q_cand;    // candidate lists, |S| per query, work items, partial lists
 
     int64_t device_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (created on first use)
@@ -114,6 +118,10 @@ void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint
 
 // Nonzeros per vector of MRPT_SPARSITY_FIXED: ceil(density * d) in [1, d].
 int32_t fixed_nonzeros(float density, int32_t d);
+
+// Most work items (chunks of its candidate list) that the candidate search
+// makes of one query; long lists get longer chunks.
+constexpr int CAND_ITEMS_MAX = 128;
 
 // Ids whose 8-bit vote counters fit in shared memory at once (64 KB).
 constexpr int64_t VOTE_CHUNK_IDS = 65536;
@@ -171,9 +179,8 @@ struct QueryLaunch {
     float *stage_ms;       // optional host float[4]
     int32_t path;          // 0: vote/emit + candidate search, 1: one fused kernel
     int32_t *cand_list;    // m x capq candidate lists (path 0)
-    int32_t capq;
+    int32_t capq;          // >= |S| of any query: T ceil(n / 2^l) / v, at most n
     int32_t *ncand;        // m (path 0)
-    int32_t *overflow;     // m (path 0)
     int2 *items;           // m x max_items_q (query, chunk) work items (path 0)
     int32_t chunk;         // candidates per work item
     int32_t max_items_q;

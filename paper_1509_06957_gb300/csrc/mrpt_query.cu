@@ -19,8 +19,7 @@
 //                   sorted top-k (knn(q, k, S) of Algorithm 4).
 //   k_vote_search   the one-kernel variant (votes, then distances of the
 //                   ids each warp emitted, then a merge of the warps'
-//                   lists); it also answers queries whose S overflows the
-//                   list capacity.
+//                   lists).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -678,8 +677,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity; false if it ran out.
 constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 21;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < MBAR_SPIN_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = MBAR_SPIN_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -863,8 +863,6 @@ struct VoteSearchArgs {
     uint32_t *work;
     int32_t cnt_words;     // counter words per chunk (<= CH_WORDS, multiple of 4)
     int32_t region_bytes;  // bytes of the counter / merge region (multiple of 16)
-    const int32_t *qlist;        // optional: process only these queries ...
-    const uint32_t *qlist_len;   // ... this many of them (read on the device)
     const QueryRecord *rec;      // plan mode: Q, outputs and m of the batch
     // vote layout (n <= 65,536): voted as in k_vote_flat
     const int4 *leaf4;
@@ -928,13 +926,7 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
     for (;;) {
         if (tid == 0) {
             const uint32_t w = atomicAdd(a.work, 1u);
-            int64_t q = -1;
-            if (a.qlist != nullptr) {
-                if (w < *a.qlist_len) q = a.qlist[w];
-            } else if (int64_t(w) < a.m) {
-                q = int64_t(w);
-            }
-            s_q = q;
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
             s_total = 0ull;
         }
         __syncthreads();
@@ -1227,12 +1219,11 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
 //                16-byte load per lane, windows balanced over the warps) and
 //                writes each query's candidate set S to a per-query list in
 //                global memory; it carries no distance state, so a block
-//                has 16 warps.
-//   k_cand_knn   one warp per query: exact distances of the listed
-//                candidates (128-bit row loads, two rows in flight) and the
-//                warp's sorted top-k, written straight to the output row.
-// Queries whose |S| exceeds the list capacity are appended to an overflow
-// list and answered by k_vote_search, which needs no list.
+//                has 16 warps.  A list holds T ceil(n / 2^l) / v entries,
+//                the most S can have (Sec. III-B), so every query fits.
+//   k_cand_knn   one warp per (query, chunk of the list) work item: exact
+//                distances of the chunk's candidates and the warp's sorted
+//                top-k; the item that completes a query merges the lists.
 
 constexpr int VE_THREADS = 512;
 constexpr int VE_WARPS = VE_THREADS / 32;
@@ -1246,11 +1237,9 @@ struct VoteEmitArgs {
     const int32_t *leaf_ids;
     int64_t m;
     int32_t v;
-    int32_t *cand;         // m x capq candidate ids
+    int32_t *cand;         // m x capq candidate ids (capq >= |S| of every query)
     int32_t capq;
     int32_t *ncand;        // m: |S|
-    int32_t *overflow;     // queries with |S| > capq
-    uint32_t *n_overflow;
     uint32_t *work;
     int32_t cnt_words;
     uint8_t *dbg_votes;
@@ -1270,6 +1259,29 @@ struct VoteEmitArgs {
     uint64_t win_magic;    // ceil(2^32 / win): i / win = (i * win_magic) >> 32 for i < 256 * win
     int32_t sentinel;
 };
+
+// Work items of the candidate search for a query with c candidates: chunks
+// of item_size(c) consecutive list entries, at least `chunk` and at most
+// CAND_ITEMS_MAX chunks per query (one item even when S is empty, so that
+// the row gets its padding).  item_count(c) * item_size(c) >= c and every
+// item holds at least one candidate when c > 0.
+__device__ __forceinline__ int item_size(int c, int chunk) {
+    return max(chunk, (c + CAND_ITEMS_MAX - 1) / CAND_ITEMS_MAX);
+}
+__device__ __forceinline__ int item_count(int c, int csz) { return c == 0 ? 1 : (c + csz - 1) / csz; }
+
+// Called by one thread once a query's votes are all in: records |S| and
+// appends the query's work items.  capq bounds |S| (|S| <= T ceil(n / 2^l) / v,
+// Sec. III-B), so the list always held every candidate.
+__device__ __forceinline__ void publish_items(const VoteEmitArgs &a, int64_t qi, int c) {
+    a.ncand[qi] = c;
+    if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
+    const int cc = min(c, a.capq);
+    const int nch = item_count(cc, item_size(cc, a.chunk));
+    const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
+    for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
+    a.done[qi] = 0;
+}
 
 // Per query (one block, queries taken from an atomic counter):
 //   1. the query's leaf in each tree gives one segment of that tree's leaf
@@ -1464,18 +1476,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
         }
         if (tid == 0) {
             const int c = s_cnt;
-            a.ncand[qi] = c;
-            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
-            if (c > a.capq) {
-                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
-            } else {
-                // work items of the candidate search: chunks of the list (one
-                // even when S is empty, so that the row gets its padding)
-                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
-                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
-                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
-                a.done[qi] = 0;
-            }
+            publish_items(a, qi, c);
         }
     }
 }
@@ -1631,18 +1632,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
         }
         if (tid == 0) {
             const int c = s_cnt;
-            a.ncand[qi] = c;
-            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
-            if (c > a.capq) {
-                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
-            } else {
-                // work items of the candidate search: chunks of the list (one
-                // even when S is empty, so that the row gets its padding)
-                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
-                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
-                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
-                a.done[qi] = 0;
-            }
+            publish_items(a, qi, c);
         }
     }
 }
@@ -1771,16 +1761,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
         }
         if (tid == 0) {
             const int c = s_cnt;
-            a.ncand[qi] = c;
-            if (a.dbg_ncand != nullptr) a.dbg_ncand[qi] = c;
-            if (c > a.capq) {
-                a.overflow[atomicAdd(a.n_overflow, 1u)] = int32_t(qi);
-            } else {
-                const int nch = c == 0 ? 1 : (c + a.chunk - 1) / a.chunk;
-                const uint32_t b0 = atomicAdd(a.n_items, uint32_t(nch));
-                for (int j = 0; j < nch; ++j) a.items[b0 + j] = make_int2(int32_t(qi), j);
-                a.done[qi] = 0;
-            }
+            publish_items(a, qi, c);
         }
         qi = qn;
     }
@@ -1816,6 +1797,8 @@ struct CandKnnArgs {
     float *part_d;         // partial top-k lists: m x max_items_q x k
     int32_t *part_i;
     const QueryRecord *rec;  // plan mode: Q, outputs and m of the batch
+    uint32_t wait_tries;   // tries of each row wait of the distance loop (a test
+                           // shortens it so that the wait runs out)
 };
 
 template <int KR>
@@ -1840,8 +1823,7 @@ __global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs 
         if (lane == 0) qi = int64_t(atomicAdd(a.work, 1u));
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= a.m) break;
-        const int c = a.ncand[qi];
-        if (c > a.capq) continue;  // answered by the overflow pass
+        const int c = min(a.ncand[qi], a.capq);
         for (int i = lane; i < a.dpad; i += 32) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
         __syncwarp();
         WarpTopK<KR> top;
@@ -1935,7 +1917,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     int call = 0;
     if (w < n_items) {
         item = a.items[w];
-        call = a.ncand[item.x];
+        call = min(a.ncand[item.x], a.capq);
     }
     for (;;) {
         if (w >= n_items) break;
@@ -1943,9 +1925,10 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
         const int ch = item.y;
         uint32_t w_next = 0;
         if (lane == 0) w_next = atomicAdd(a.work, 1u);
-        const int nch = call == 0 ? 1 : (call + a.chunk - 1) / a.chunk;
-        const int lo = ch * a.chunk;
-        const int c = min(call, lo + a.chunk) - lo;  // candidates of this item
+        const int csz = item_size(call, a.chunk);
+        const int nch = item_count(call, csz);
+        const int lo = ch * csz;
+        const int c = min(call, lo + csz) - lo;  // candidates of this item
         if (qi != staged_q) {
             __syncwarp();
             if (qvec) {
@@ -1996,8 +1979,8 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
             const int32_t id0 = cid[j - cbase];
             const int32_t id1 = two ? cid[j + 1 - cbase] : id0;
             // warp-uniform outcome of the bounded waits
-            bool ok = mbar_wait(&bar[slot], (parity >> slot) & 1u);
-            if (two) ok = mbar_wait(&bar[slot1], (parity >> slot1) & 1u) && ok;
+            bool ok = mbar_wait(&bar[slot], (parity >> slot) & 1u, a.wait_tries);
+            if (two) ok = mbar_wait(&bar[slot1], (parity >> slot1) & 1u, a.wait_tries) && ok;
             if (!__all_sync(0xffffffffu, ok)) {
                 failed = true;
                 break;
@@ -2151,7 +2134,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
         w = __shfl_sync(0xffffffffu, w_next, 0);
         if (w < n_items) {
             item = a.items[w];
-            call = a.ncand[item.x];
+            call = min(a.ncand[item.x], a.capq);
         }
     }
     if (failed && lane == 0) {
@@ -2371,9 +2354,7 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.cand = ql.cand_list;
     a.capq = ql.capq;
     a.ncand = ql.ncand;
-    a.overflow = ql.overflow;
     uint32_t *ctr = ql.counters ? ql.counters : idx->status;
-    a.n_overflow = ctr + 3;
     a.work = ctr + 1;
     a.rec = ql.rec;
     a.cnt_words = cnt_words;
@@ -2442,6 +2423,7 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.done = ql.done;
     a.part_d = ql.part_d;
     a.part_i = ql.part_i;
+    a.wait_tries = debug_row_wait_tries();
     int sms = 0, per_sm = 0;
     cudaError_t e;
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
@@ -2463,26 +2445,6 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     const int64_t blocks = std::max<int64_t>(
         1, std::min<int64_t>((ql.m + CK_WARPS - 1) / CK_WARPS, int64_t(sms) * std::max(per_sm, 1)));
     k_cand_knn_regs<KR><<<unsigned(blocks), CK_THREADS, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-// k_vote_search over the overflow list (its length is read on the device).
-template <int KR>
-cudaError_t launch_overflow(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
-    VoteSearchArgs a;
-    size_t smem = 0;
-    int64_t blocks = 0;
-    QueryLaunch q2 = ql;
-    q2.votes = nullptr;
-    q2.n_cand = nullptr;
-    q2.cand = nullptr;
-    uint32_t *ctr = ql.counters ? ql.counters : idx->status;
-    cudaError_t e = plan_vote<KR>(idx, q2, ctr + 4, a, smem, blocks);
-    if (e != cudaSuccess) return e;
-    a.qlist = ql.overflow;
-    a.qlist_len = ctr + 3;
-    a.rec = ql.rec;
-    k_vote_search<KR><<<unsigned(blocks), VS_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -2523,8 +2485,8 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
         if (e != cudaSuccess) return cuda_fail(e, "k_vote_search");
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
     } else {
-        // work counters [1] vote/emit, [2] candidate search, [3] overflow
-        // length, [4] overflow pass, [5] candidate-search work items
+        // work counters [1] vote/emit, [2] candidate search, [3], [4]
+        // unused, [5] candidate-search work items
         MRPT_CUDA_TRY(cudaMemsetAsync((ql.counters ? ql.counters : idx->status) + 1, 0,
                                       5 * sizeof(uint32_t), s));
         e = launch_vote_emit(idx, ql, s);
@@ -2561,15 +2523,6 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
             e = launch_cand_knn<8, 0>(idx, ql, s);
         }
         if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
-        if (kr <= 1)
-            e = launch_overflow<1>(idx, ql, s);
-        else if (kr <= 2)
-            e = launch_overflow<2>(idx, ql, s);
-        else if (kr <= 4)
-            e = launch_overflow<4>(idx, ql, s);
-        else
-            e = launch_overflow<8>(idx, ql, s);
-        if (e != cudaSuccess) return cuda_fail(e, "k_vote_search (overflow)");
     }
     if (ql.stage_ms) {
         MRPT_CUDA_TRY(cudaEventRecord(idx->ev[3], s));

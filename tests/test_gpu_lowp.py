@@ -116,3 +116,46 @@ def test_fp8_rerank(mr, gen):
         hits += len(set(got.tolist()) & set(oi[i][fin[i]].tolist()))
     assert hits / fin.sum() >= 0.97
     idx.close()
+
+
+@pytest.mark.parametrize("prec,margin,min_recall", [(1, 8, 0.99), (2, 8, 0.97), (2, 32, 0.99)],
+                         ids=["bf16-m8", "fp8-m8", "fp8-m32"])
+def test_large_candidate_sets_reduced_precision(mr, prec, margin, min_recall):
+    """|S| of about 13,000 per query (T = 40, depth 4, v = 2: the bound
+    T ceil(n / 2^l) / v is 50,000): every query goes through the batched
+    candidate search -- (query, chunk) work items over the whole list, rows
+    from the reduced-precision copy, float32 re-rank of the k + margin
+    survivors -- and is checked against the oracle: ids in S, exact float32
+    distances, ascending rows, tie-aware recall at least min_recall (the
+    bounds sit below a float64 emulation of the same rounding: 1.0, 0.995,
+    1.0).  |S| is checked against the oracle for every query."""
+    from _parity import check_lowp_results
+    X, Q = workloads.latent_factor(20000, 96, 300, seed=3)
+    T, l, v, k = 40, 4, 2, 10
+    dens = float(np.float32(96 ** -0.5))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, dens, 5)
+    mr.mrpt_add_lowp(idx, prec)
+    ids, d, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, precision=prec,
+                                   margin=margin, debug=True, cand_cap=1)
+    torch.cuda.synchronize()
+    ref = oracle.grow_trees(X, T, l, dens, 5)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, k, v, want_internals=True)
+    ncand = dbg["n_cand"].cpu().numpy()
+    assert np.array_equal(ncand, oncand)
+    assert ncand.min() > 2048
+    check_lowp_results(X, Q, ids.cpu().numpy(), d.cpu().numpy(), oi, od, oracle_sets(ref, oleaf, v),
+                       min_recall)
+    idx.close()
+
+
+def test_large_candidate_sets_float32_match_oracle(mr):
+    """The same |S| > 2,048 queries in float32: the oracle's rows exactly."""
+    X, Q = workloads.latent_factor(20000, 96, 300, seed=3)
+    T, l, v, k = 40, 4, 2, 10
+    dens = float(np.float32(96 ** -0.5))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, dens, 5)
+    ids, d = _query(mr, idx, Q, k, v)
+    ref = oracle.grow_trees(X, T, l, dens, 5)
+    oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, want_internals=True)
+    check_results(X, Q, ids, d, oi, od, oracle_sets(ref, oleaf, v))
+    idx.close()

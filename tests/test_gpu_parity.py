@@ -85,11 +85,12 @@ def test_k_values_and_padding(mr, k, path):
     _full_check(mr, X, Q, 5, 3, k, 2, 0.3, 5, path=path)
 
 
-def test_overflowing_candidate_lists(mr):
-    """|S| above the per-query list capacity (2,048): those queries are
-    answered by the fused kernel inside the same call."""
+@pytest.mark.parametrize("path", PATHS)
+def test_candidate_sets_of_thousands(mr, path):
+    """v = 1 on two-leaf trees: |S| of several thousand per query, all in
+    the candidate lists (sized T ceil(n / 2^l) / v) and work items."""
     X, Q = workloads.gaussian_mixture(6000, 12, 20, n_centres=3, seed=12)
-    _full_check(mr, X, Q, 6, 1, 10, 1, 0.5, 3)
+    _full_check(mr, X, Q, 6, 1, 10, 1, 0.5, 3, path=path)
 
 
 def test_ragged_dimension_and_host_buffers(mr):
@@ -232,4 +233,26 @@ def test_injected_allocation_failure(mr):
     idx = mr.mrpt_build(X, 3, 3, 0.5, 0)  # the library is still usable
     ids, _ = mr.mrpt_query(idx, X[:4], 3, 1)
     assert ids[:, 0].tolist() == [0, 1, 2, 3]
+    idx.close()
+
+
+def test_batch_beyond_the_candidate_scratch_budget(mr):
+    """v = 1 on two trees of depth 1 over 60,000 points: the list capacity
+    is n = 60,000 per query, so 9,000 queries need more candidate scratch
+    than one launch may use (2 GiB) and run as consecutive sub-batches.
+    Every row equals the oracle's; stage times are the sum over them."""
+    X, Q = workloads.gaussian_mixture(60000, 8, 9000, n_centres=40, seed=31)
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 2, 1, 0.5, 8)
+    stage = np.zeros(4, np.float32)
+    ids, dists = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), 10, 1, stage_ms=stage)
+    torch.cuda.synchronize()
+    assert stage[3] > 0 and stage[1] > 0 and stage[2] > 0
+    ref = oracle.grow_trees(X, 2, 1, 0.5, 8)
+    check_index_parity(idx, mr, ref)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, 10, 1, want_internals=True)
+    assert oncand.min() > 30000
+    gi, gd = ids.cpu().numpy(), dists.cpu().numpy()
+    diff = np.nonzero((gi != oi).any(1))[0]
+    sets = dict(zip(diff.tolist(), oracle_sets(ref, oleaf[diff], 1)))
+    check_results(X, Q, gi, gd, oi, od, [sets.get(i, set()) for i in range(len(Q))])
     idx.close()
