@@ -535,34 +535,62 @@ __global__ void k_pad_leaves(const int32_t *__restrict__ leaf_ids, int64_t n, in
     }
 }
 
-// Each 128-id window of a padded leaf (the ids one warp votes with four
-// atomics, lane r taking window positions 4r..4r+3) is reordered by counter
-// bank ((id >> 2) mod 32, stable).  Atomic u of the warp then takes the ids
-// of ranks u, u+4, u+8, ... in bank order, so ids of one bank spread over
-// the four atomics instead of queueing in one.  One thread per window.
-__global__ void k_bank_order_windows(int32_t *__restrict__ leaf4, int32_t T,
-                                     const int32_t *__restrict__ off4, int64_t L, int64_t s4,
-                                     int32_t win) {
+// Spreads the entries of each 256-entry window of a padded leaf over counter
+// banks.  A warp votes a window with eight shared-memory reductions: lane r
+// takes its entries 4r..4r+3 of each 128-entry half h, and reduction (h, u)
+// updates window positions 128h + 4r + u for r = 0..31.  Counter bank of id x
+// is (x >> 2) mod 32; two lanes of one reduction in the same bank cost an
+// extra pass.  Each reduction is therefore given ids of distinct banks while
+// it can, always from the banks with the most entries left (so that the
+// crowded banks spread over all eight).  Votes do not depend on the order, so
+// only the layout changes.  One thread per window; build-time only.
+__global__ void k_bank_spread_windows(int32_t *__restrict__ leaf4, int32_t T,
+                                      const int32_t *__restrict__ off4, int64_t L, int64_t s4,
+                                      int32_t win) {
     const int64_t total = int64_t(T) * L * win;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
          g += int64_t(gridDim.x) * blockDim.x) {
         const int64_t t = g / (L * win);
-        const int64_t r = g - t * L * win;
-        const int64_t j = r / win;
-        const int32_t w = int32_t(r - j * win);
+        const int64_t r0 = g - t * L * win;
+        const int64_t j = r0 / win;
+        const int32_t w = int32_t(r0 - j * win);
         const int32_t len4 = off4[j + 1] - off4[j];
-        if (32 * w >= len4) continue;
-        const int32_t n4 = min(32, len4 - 32 * w);
-        int32_t *base = leaf4 + 4 * (t * s4 + off4[j] + 32 * w);
-        int32_t ids[128];
-        int32_t cnt[33];
-        for (int b = 0; b <= 32; ++b) cnt[b] = 0;
-        for (int e = 0; e < 4 * n4; ++e) {
-            ids[e] = base[e];
-            ++cnt[((ids[e] >> 2) & 31) + 1];
+        if (64 * w >= len4) continue;
+        const int32_t n4 = min(64, len4 - 64 * w);
+        int32_t *base = leaf4 + 4 * (t * s4 + off4[j] + 64 * int64_t(w));
+        int32_t byb[256];   // entries grouped by bank
+        int32_t start[33];
+        int32_t rem[32];
+        for (int b = 0; b <= 32; ++b) start[b] = 0;
+        for (int e = 0; e < 4 * n4; ++e) ++start[((base[e] >> 2) & 31) + 1];
+        for (int b = 0; b < 32; ++b) start[b + 1] += start[b];
+        for (int b = 0; b < 32; ++b) rem[b] = start[b + 1] - start[b];
+        {
+            int32_t fill[32];
+            for (int b = 0; b < 32; ++b) fill[b] = start[b];
+            for (int e = 0; e < 4 * n4; ++e) {
+                const int32_t x = base[e];
+                byb[fill[(x >> 2) & 31]++] = x;
+            }
         }
-        for (int b = 0; b < 32; ++b) cnt[b + 1] += cnt[b];
-        for (int e = 0; e < 4 * n4; ++e) base[cnt[(ids[e] >> 2) & 31]++] = ids[e];
+        for (int h = 0; h < 2; ++h) {
+            const int cap = max(0, min(32, n4 - 32 * h));
+            for (int u = 0; u < 4; ++u) {
+                uint32_t used = 0u;
+                for (int r = 0; r < cap; ++r) {
+                    int best = -1, best_any = -1;
+                    for (int b = 0; b < 32; ++b) {
+                        if (rem[b] == 0) continue;
+                        if (best_any < 0 || rem[b] > rem[best_any]) best_any = b;
+                        if (!((used >> b) & 1u) && (best < 0 || rem[b] > rem[best])) best = b;
+                    }
+                    const int b = best >= 0 ? best : best_any;
+                    --rem[b];
+                    used |= 1u << b;
+                    base[128 * h + 4 * r + u] = byb[start[b] + rem[b]];
+                }
+            }
+        }
     }
 }
 
@@ -599,11 +627,11 @@ int build_vote_layout(mrpt_index *idx) {
                                                        reinterpret_cast<int32_t *>(idx->leaf4));
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            const int64_t windows = int64_t(idx->T) * L * idx->vote_win;
+            const int32_t win256 = (idx->vote_win + 1) / 2;
+            const int64_t windows = int64_t(idx->T) * L * win256;
             const int wblocks = int(std::min<int64_t>((windows + 127) / 128, 152 * 16));
-            k_bank_order_windows<<<wblocks, 128, 0, idx->stream>>>(reinterpret_cast<int32_t *>(idx->leaf4),
-                                                                  idx->T, idx->leaf_off4, L, s4,
-                                                                  idx->vote_win);
+            k_bank_spread_windows<<<wblocks, 128, 0, idx->stream>>>(reinterpret_cast<int32_t *>(idx->leaf4),
+                                                                   idx->T, idx->leaf_off4, L, s4, win256);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);

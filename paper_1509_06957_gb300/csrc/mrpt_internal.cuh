@@ -79,8 +79,9 @@ struct mrpt_index {
     int32_t *leaf_ids = nullptr; // T x n
     // Vote layout (only when n <= VOTE_CHUNK_IDS): leaf j of tree t starts at
     // int4 index t*vote_s4 + leaf_off4[j] and holds the leaf's ids, then the
-    // sentinel id up to a multiple of 4; each 128-id window is ordered by
-    // counter bank ((id >> 2) mod 32).
+    // sentinel id up to a multiple of 4; within each 256-entry window the ids
+    // are placed so that each of a warp's eight vote reductions meets as many
+    // distinct counter banks ((id >> 2) mod 32) as the window allows.
     int4 *leaf4 = nullptr;
     int32_t *leaf_off4 = nullptr; // L + 1
     int64_t vote_s4 = 0;          // int4s per tree

@@ -1637,28 +1637,91 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
     }
 }
 
+// One lane's four entries e.x..e.w of a vote window: each adds one vote to
+// its 8-bit counter (byte id & 3 of word id >> 2 at shared address cnt_s);
+// with ok == 0 the four votes go to the lane's own spare word at shared
+// address spare instead (a select: predicated shared atomics cost a branch
+// each).  The increment 1 << 8 (id & 3) is one byte permute (prmt.b4e of
+// the word 1 selected by id & 3), and so is the old count of the entry's
+// byte (prmt.f4e moves byte id & 3 of the old word to byte 0).  x receives
+// the four old counts, entry u in byte u, each XOR v-1: a zero byte marks an
+// entry whose count went from v-1 to v (x is unspecified when ok == 0).  The
+// result is nonzero when ok != 0 and x has a zero byte, tested word-wide:
+// (x - 0x01010101) & ~x & 0x80808080 is nonzero iff some byte of x is zero.
+__device__ __forceinline__ uint32_t vote4h(uint32_t cnt_s, int4 e, uint32_t ok, uint32_t vm1x4,
+                                           uint32_t spare, uint32_t &x) {
+    uint32_t hit;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h;\n\t"
+        ".reg .b32 t<4>, n<4>, r<4>, z, one;\n\t"
+        "setp.ne.u32 p, %6, 0;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "mov.b32 one, 1;\n\t"
+        "prmt.b32.b4e n0, one, z, %2;\n\t"
+        "prmt.b32.b4e n1, one, z, %3;\n\t"
+        "prmt.b32.b4e n2, one, z, %4;\n\t"
+        "prmt.b32.b4e n3, one, z, %5;\n\t"
+        "and.b32 t0, %2, 0xfffffffc;\n\t"
+        "and.b32 t1, %3, 0xfffffffc;\n\t"
+        "and.b32 t2, %4, 0xfffffffc;\n\t"
+        "and.b32 t3, %5, 0xfffffffc;\n\t"
+        "add.u32 t0, t0, %7;\n\t"
+        "add.u32 t1, t1, %7;\n\t"
+        "add.u32 t2, t2, %7;\n\t"
+        "add.u32 t3, t3, %7;\n\t"
+        "selp.b32 t0, t0, %9, p;\n\t"
+        "selp.b32 t1, t1, %9, p;\n\t"
+        "selp.b32 t2, t2, %9, p;\n\t"
+        "selp.b32 t3, t3, %9, p;\n\t"
+        "atom.shared.add.u32 r0, [t0], n0;\n\t"
+        "atom.shared.add.u32 r1, [t1], n1;\n\t"
+        "atom.shared.add.u32 r2, [t2], n2;\n\t"
+        "atom.shared.add.u32 r3, [t3], n3;\n\t"
+        "prmt.b32.f4e r0, r0, z, %2;\n\t"
+        "prmt.b32.f4e r1, r1, z, %3;\n\t"
+        "prmt.b32.f4e r2, r2, z, %4;\n\t"
+        "prmt.b32.f4e r3, r3, z, %5;\n\t"
+        "prmt.b32 r0, r0, r1, 0x0040;\n\t"
+        "prmt.b32 r2, r2, r3, 0x0040;\n\t"
+        "prmt.b32 r0, r0, r2, 0x5410;\n\t"
+        "xor.b32 %1, r0, %8;\n\t"
+        "sub.u32 r1, %1, 0x01010101;\n\t"
+        "not.b32 r2, %1;\n\t"
+        "and.b32 r1, r1, r2;\n\t"
+        "and.b32 r1, r1, 0x80808080;\n\t"
+        "setp.ne.and.u32 h, r1, 0, p;\n\t"
+        "selp.u32 %0, 1, 0, h;\n\t"
+        "}"
+        : "=r"(hit), "=r"(x)
+        : "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(ok), "r"(cnt_s), "r"(vm1x4), "r"(spare)
+        : "memory");
+    return hit;
+}
+
 // k_vote_emit for an index whose ids fit one counter array (n <= 65,536),
 // over the vote layout: every leaf starts on a 16-byte boundary and is padded
 // with the sentinel to a multiple of 4 ids, so a lane's 16-byte load is four
-// ids of one leaf (or lies past the leaf and votes nothing), and every leaf
-// spans the same number of 128-entry windows (a.win).  Window i of the query
-// is window i % win of tree i / win; warps take contiguous runs of windows.
+// ids of one leaf (or lies past the leaf and votes nothing).  A window is 256
+// entries of one leaf (two 16-byte loads per lane, 64 apart in 16-byte
+// units); every leaf spans the same number a.win of windows, and window i of
+// the query is window i % win of tree i / win.  Warp w takes windows w,
+// w + 16, w + 32, ... two at a time (four loads in flight before any vote).
 __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs a0) {
     VoteEmitArgs a = a0;
     if (a.rec != nullptr) a.m = a.rec->m;
     extern __shared__ __align__(16) unsigned char smem[];
-    // cnt_words counter words, the sentinel's word (+3 unused), a spare word
-    // per lane
+    // cnt_words counter words, the sentinel's word (+35 unused), then per
+    // tree (first 16-byte unit of the query's leaf, its 16-byte units)
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);
-    int64_t *sbase = reinterpret_cast<int64_t *>(cnt + a.cnt_words + 36);  // per tree: first int4
-    int32_t *slen = reinterpret_cast<int32_t *>(sbase + a.T_use);        // per tree: int4s
+    int2 *seg = reinterpret_cast<int2 *>(cnt + a.cnt_words + 36);
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
-    __shared__ int s_win;  // next window of the query
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const uint32_t vm1 = uint32_t(a.v - 1);
+    const int warp = tid >> 5;
+    const uint32_t vm1x4 = uint32_t(a.v - 1) * 0x01010101u;
     const int T = a.T_use;
     const int K = a.win;
     const int W = T * K;
@@ -1681,10 +1744,9 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
         pf_e = a.leaf_off4[lf + 1];
     }
     while (qi >= 0) {
-        if (tid < T) {
-            sbase[tid] = int64_t(tid) * a.s4 + pf_o;
-            slen[tid] = pf_e - pf_o;
-        }
+        // tree t's leaf starts at 16-byte unit t * s4 + off4 (< 2^31: T s4 is
+        // at most 255 (n / 4 + 2^l) for n <= 65,536)
+        if (tid < T) seg[tid] = make_int2(int32_t(int64_t(tid) * a.s4) + pf_o, pf_e - pf_o);
         {
             uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
             const int n4 = a.cnt_words >> 2;
@@ -1694,53 +1756,41 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
             const uint32_t w = atomicAdd(a.work, 1u);
             s_q = int64_t(w) < a.m ? int64_t(w) : -1;
             s_cnt = 0;
-            s_win = 0;
         }
         __syncthreads();
         const int64_t qn = s_q;
         int32_t pf_lf = 0;
         if (qn >= 0 && tid < T) pf_lf = __ldg(a.leaf_of_q + qn * T + tid);
         int32_t *clist = a.cand + qi * int64_t(a.capq);
-        auto emit = [&](const int4 &q, uint32_t emask) {
-            const int32_t e[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (((emask >> u) & 1u) && e[u] != a.sentinel) {
-                    const int slot = atomicAdd(&s_cnt, 1);
-                    if (slot < a.capq) clist[slot] = e[u];
-                    if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = e[u];
-                }
+        // rare path: append the entries whose count reached v (Algorithm 4's
+        // emission; the sentinel is never a candidate).  Bit 7 of byte u of
+        // zb is set iff byte u of x is zero.
+        auto emit = [&](const int4 &q, uint32_t x) {
+            uint32_t zb = ~(((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x | 0x7f7f7f7fu);
+            while (zb != 0u) {
+                const int u = (__ffs(int(zb)) - 1) >> 3;
+                zb &= zb - 1u;
+                const int32_t id = u == 0 ? q.x : u == 1 ? q.y : u == 2 ? q.z : q.w;
+                if (id == a.sentinel) continue;
+                const int slot = atomicAdd(&s_cnt, 1);
+                if (slot < a.capq) clist[slot] = id;
+                if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = id;
             }
         };
-        // warps claim four windows at a time from a shared counter (so they
-        // finish together); all four loads are in flight before any votes,
-        // and a window past W votes nothing
-        for (;;) {
-            int i = 0;
-            if (lane == 0) i = atomicAdd(&s_win, 4);
-            i = __shfl_sync(0xffffffffu, i, 0);
-            if (i >= W) break;
-            int t = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32), k = i - t * K;
-            int4 q[4];
-            uint32_t ok[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int tc = t < T ? t : T - 1;
-                const int32_t j = k * 32 + lane;
-                ok[r] = (i + r < W && j < slen[tc]) ? 1u : 0u;
-                q[r] = ldg4_if(a.leaf4 + sbase[tc] + j, ok[r]);
-                k = k + 1 == K ? 0 : k + 1;
-                t = k == 0 ? t + 1 : t;
-            }
-            uint32_t em[4], any = 0u;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                em[r] = vote4p(cnt_s, q[r], ok[r], spare, vm1);
-                any |= em[r];
-            }
-            if (any != 0u) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) emit(q[r], em[r]);
+        for (int i = warp; i < W; i += VE_WARPS) {
+            const int t0 = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32);
+            const int j0 = (i - t0 * K) * 64 + lane;
+            const int2 s0 = seg[t0];
+            const uint32_t ok00 = j0 < s0.y, ok01 = j0 + 32 < s0.y;
+            const int4 *p0 = a.leaf4 + (s0.x + j0);
+            const int4 q00 = ldg4_if(p0, ok00);
+            const int4 q01 = ldg4_if(p0 + 32, ok01);
+            uint32_t o00, o01;
+            const uint32_t h0 = vote4h(cnt_s, q00, ok00, vm1x4, spare, o00);
+            const uint32_t h1 = vote4h(cnt_s, q01, ok01, vm1x4, spare, o01);
+            if (__any_sync(0xffffffffu, (h0 | h1) != 0u)) {
+                if (h0) emit(q00, o00);
+                if (h1) emit(q01, o01);
             }
         }
         if (qn >= 0 && tid < T) {
@@ -2334,7 +2384,7 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     const int64_t chunks = (idx->n + CH_IDS - 1) / CH_IDS;
     const bool packed = !flat && leaf_len < 48 * chunks;
     auto kern = flat ? k_vote_flat : packed ? k_vote_packed : k_vote_emit;
-    const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 12
+    const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 8
                         : packed ? size_t(cnt_words + 32) * 4 + size_t(4 * ql.n_trees + 1) * 4
                                  : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
                                        size_t(4 * ql.n_trees + 1) * 4;
@@ -2369,8 +2419,10 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.leaf4 = idx->leaf4;
     a.leaf_off4 = idx->leaf_off4;
     a.s4 = idx->vote_s4;
-    a.win = idx->vote_win;
-    a.win_magic = ((uint64_t(1) << 32) + uint64_t(idx->vote_win) - 1) / uint64_t(std::max(idx->vote_win, 1));
+    // 256-entry windows per leaf (vote_win counts 128-entry ones);
+    // i / win = (i * win_magic) >> 32 for every window index i < T win
+    a.win = std::max((idx->vote_win + 1) / 2, 1);
+    a.win_magic = ((uint64_t(1) << 32) + uint64_t(a.win) - 1) / uint64_t(a.win);
     a.sentinel = vote_sentinel(idx->n);
     kern<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
