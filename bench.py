@@ -561,28 +561,65 @@ def run_build(args):
     return out
 
 
+def lowp_copy(X, prec, torch):
+    """Host-side float64 values of the library's reduced-precision copy of X
+    (mrpt_add_lowp): bfloat16 round-to-nearest-even, or e4m3 of
+    x / (max|x| / 448) per row times that scale."""
+    if prec == 1:
+        return X.bfloat16().double()
+    mx = X.abs().amax(1, keepdim=True)
+    scale = torch.where(mx > 0, mx / 448.0, torch.ones_like(mx))
+    q = (X * (1.0 / scale)).clamp(-448.0, 448.0).to(torch.float8_e4m3fn)
+    return q.double() * scale.double()
+
+
+def lowp_distance_error(X, Xl, Q, ids, torch):
+    """Relative error of the squared distances computed from the reduced
+    copy Xl (in float64, so only its rounding counts) against the exact
+    float64 squared distances, over the returned neighbours (ids >= 0):
+    (max, mean)."""
+    errs = []
+    for s0 in range(0, Q.shape[0], 256):
+        a = ids[s0:s0 + 256].long()
+        ok = a >= 0
+        a = a.clamp(min=0)
+        q = Q[s0:s0 + 256].double()[:, None, :]
+        d64 = ((X[a].double() - q) ** 2).sum(2)
+        dl = ((Xl[a] - q) ** 2).sum(2)
+        good = ok & (d64 > 0)
+        errs.append(((dl - d64).abs() / d64.clamp(min=1e-300))[good])
+    e = torch.cat(errs)
+    return (float(e.max()), float(e.mean())) if e.numel() else (0.0, 0.0)
+
+
 def run_large(args):
-    """--workload large: queries on the 1M-point configurations.
-    - 1M x 128 heavy-tailed integers (lognormal-int), 10,000 queries, k = 100,
-      T = 100, l = 12; float32 and bfloat16 + float32 re-rank of the top 132;
+    """--workload large: the v sweep per precision on the synthetic stand-ins.
+    - mnist-like 60,000 x 784 (integers 0..255, exact in bfloat16),
+      10,000 queries, k = 10, T = 100, l = 8;
+    - 1M x 128 heavy-tailed integers (lognormal-int), 10,000 queries,
+      k = 100, T = 100, l = 12;
     - 1M x 960 rank-64 factors (latent-factor), 1,000 queries, k = 10,
-      T = 200, l = 10; float32, bfloat16 and e4m3 rows with re-rank.
-    v is swept over 1..10.  Each point reports tie-aware recall@k against a
-    float64 brute force and queries/s of device time (L2 flushed before the
-    timed pass)."""
+      T = 200, l = 10.
+    Precisions: float32, bfloat16 and e4m3 rows, each with a float32 re-rank
+    of the k + 32 nearest (skipped for a lossless bfloat16 copy).  Each point
+    reports tie-aware recall@k against a float64 brute force, the recall loss
+    against float32 at the same v, the relative error of the reduced copy's
+    squared distances against float64 at the returned neighbours (max, mean)
+    and queries/s of device time (L2 flushed before the timed pass)."""
     import torch
     import paper_1509_06957_gb300 as mr
     dev = torch.device("cuda", 0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stage = np.zeros(4, np.float32)
-    confs = [("lognormal-int 1000000x128, 10000 queries", workloads.lognormal_int, 128, 10000, 100, 100, 12,
-              [(0, 0), (1, 32)]),
-             ("latent-factor 1000000x960, 1000 queries", workloads.latent_factor, 960, 1000, 10, 200, 10,
-              [(0, 0), (1, 32), (2, 32)])]
-    out = {"metric": "queries/s and tie-aware recall@k on the 1M-point configurations (device time)",
+    confs = [("mnist-like 60000x784, 10000 queries", lambda n, d, m, seed: workloads.mnist_like(n, m, seed=seed),
+              60000, 784, 10000, 10, 100, 8),
+             ("lognormal-int 1000000x128, 10000 queries", workloads.lognormal_int, 1_000_000, 128, 10000, 100, 100, 12),
+             ("latent-factor 1000000x960, 1000 queries", workloads.latent_factor, 1_000_000, 960, 1000, 10, 200, 10)]
+    precs = [(0, 0), (1, 32), (2, 32)]
+    out = {"metric": "queries/s, tie-aware recall@k and reduced-precision distance error per v (device time)",
            "data": "synthetic", "configs": []}
-    for name, gen, d, m, k, T, l, precs in confs:
-        X_np, Q_np = gen(1_000_000, d, m, seed=0)
+    for name, gen, n, d, m, k, T, l in confs[: args.large_configs]:
+        X_np, Q_np = gen(n, d, m, seed=0)
         X, Q = torch.from_numpy(X_np).to(dev), torch.from_numpy(Q_np).to(dev)
         del X_np, Q_np
         gt_ids, _ = exact_knn_gpu(X, Q, k, torch)
@@ -590,22 +627,36 @@ def run_large(args):
                          for s in range(0, m, 64)]).float()[:, None]
         index = mr.mrpt_build(X, T, l, 0.0, seed=0)
         mr.mrpt_add_lowp(index, mr.MRPT_PREC_BF16)
-        if any(p == 2 for p, _ in precs):
-            mr.mrpt_add_lowp(index, mr.MRPT_PREC_FP8)
+        mr.mrpt_add_lowp(index, mr.MRPT_PREC_FP8)
+        bf16_exact = bool(torch.equal(X, X.bfloat16().float()))
+        lows = {1: lowp_copy(X, 1, torch), 2: lowp_copy(X, 2, torch)}
         rows = []
         for v in range(1, 11):
+            rec32 = None
             for prec, margin in precs:
                 mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin)  # warm
                 flush.zero_()
-                _, dists = mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin, stage_ms=stage)
+                ids, dists = mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin, stage_ms=stage)
                 rec = float(((dists <= kth * (1 + 1e-5)) & torch.isfinite(dists)).sum()) / (m * k)
-                rows.append(dict(v=v, precision=("fp32", "bf16", "fp8")[prec], margin=margin,
-                                 recall=round(rec, 4), qps=round(m / (float(stage[3]) / 1e3), 1),
-                                 ms=round(float(stage[3]), 3)))
+                row = dict(v=v, precision=("fp32", "bf16", "fp8")[prec], margin=margin,
+                           recall=round(rec, 4), qps=round(m / (float(stage[3]) / 1e3), 1),
+                           ms=round(float(stage[3]), 3))
+                if prec == 0:
+                    rec32 = rec
+                else:
+                    emax, emean = lowp_distance_error(X, lows[prec], Q, ids, torch)
+                    row.update(recall_loss_vs_fp32=round(rec32 - rec, 4), dist2_rel_err_max=float(f"{emax:.3g}"),
+                               dist2_rel_err_mean=float(f"{emean:.3g}"),
+                               rerank=not (prec == 1 and bf16_exact))
+                rows.append(row)
         index.close()
-        out["configs"].append({"workload": name, "T": T, "depth": l, "k": k, "rows": rows})
-        del X, Q
+        out["configs"].append({"workload": name, "T": T, "depth": l, "k": k, "bf16_exact": bf16_exact,
+                               "rows": rows})
+        del X, Q, lows
         torch.cuda.empty_cache()
+    if args.detail_out:
+        with open(args.detail_out, "w") as f:
+            json.dump(out, f)
     print(json.dumps(out), flush=True)
     return out
 
@@ -804,6 +855,7 @@ def main():
     ap.add_argument("--workload", choices=["batch", "stream", "build", "pareto", "large"], default="batch",
                     help="batch: the 10,000-query benchmark; stream: uneven batches through plans")
     ap.add_argument("--stream-queries", type=int, default=100000)
+    ap.add_argument("--large-configs", type=int, default=3, help="large workload: how many configurations")
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp8"], default="auto",
                     help="candidate-distance precision (auto: the faster at the recall target)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1],

@@ -82,3 +82,34 @@ def test_reference_arm_last_line_parses():
     assert out["config"]["workload"] == bench.WORKLOAD["name"]
     for key in ("cpu_baseline", "e2e", "metric", "higher_is_better", "ms_per_step"):
         assert key in out
+
+
+def test_reduced_copy_emulation_and_distance_error():
+    """The host emulation of the reduced copies: bfloat16 keeps integers
+    0..255 exactly; e4m3 with the per-row scale max|x| / 448 is within
+    2^-4 relative of each value (3 mantissa bits) and keeps each row's
+    largest magnitude exactly; the distance error is zero for an exact copy
+    and matches a hand computation otherwise."""
+    import torch
+    g = torch.Generator().manual_seed(0)
+    Xi = torch.randint(0, 256, (50, 16), generator=g).float()
+    assert torch.equal(bench.lowp_copy(Xi, 1, torch), Xi.double())
+    X = torch.rand((50, 16), generator=g) * 3 - 1
+    X8 = bench.lowp_copy(X, 2, torch)
+    assert torch.all((X8 - X.double()).abs() <= X.double().abs() * 2.0 ** -4 + 1e-6)
+    big = X.abs().argmax(1)
+    rows = torch.arange(50)
+    assert torch.allclose(X8[rows, big].abs(), X.double()[rows, big].abs(), rtol=1e-6)
+    Q = torch.rand((3, 16), generator=g)
+    ids = torch.tensor([[0, 1], [2, -1], [4, 5]], dtype=torch.int32)
+    assert bench.lowp_distance_error(X, X.double(), Q, ids, torch) == (0.0, 0.0)
+    emax, emean = bench.lowp_distance_error(X, X8, Q, ids, torch)
+    want = []
+    for i, row in enumerate(ids.tolist()):
+        for j in row:
+            if j < 0:
+                continue
+            d64 = ((X[j].double() - Q[i].double()) ** 2).sum()
+            dl = ((X8[j] - Q[i].double()) ** 2).sum()
+            want.append(float(abs(dl - d64) / d64))
+    assert abs(emax - max(want)) < 1e-12 and abs(emean - sum(want) / len(want)) < 1e-12
