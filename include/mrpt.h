@@ -101,13 +101,20 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
  *       first draw being the one the Bernoulli rule compares with density,
  *       so the set is a uniformly random subset; values are the same N(0,1)
  *       draws as in the Bernoulli rule.
- * Errors: those of mrpt_build; INVALID_ARG for an unknown sparsity.
+ * Errors: those of mrpt_build; INVALID_ARG for an unknown sparsity or a tree
+ * offset out of range.
  */
 #define MRPT_SPARSITY_BERNOULLI 0
 #define MRPT_SPARSITY_FIXED 1
 
 typedef struct mrpt_build_opts {
     int32_t sparsity;
+    int32_t tree_offset;  /* t0 >= 0, t0 + T <= MRPT_MAX_TREES: the index holds trees t0 ..
+                             t0+T-1 of the random source (tree i of the index takes the
+                             draws of tree t0+i), so it equals trees t0.. of an index of
+                             t0+T trees with the same seed -- one shard of a tree-sharded
+                             index (Sec. I-C: the trees are independent and may live on
+                             different machines).  0 (default): trees 0..T-1. */
 } mrpt_build_opts;
 
 int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, float density,
@@ -256,6 +263,7 @@ typedef struct mrpt_index_info {
     uint64_t seed;
     int64_t nnz;           /* nonzeros of R over all T*l vectors */
     int64_t device_bytes;  /* device memory held (index + scratch) */
+    int32_t tree_offset;   /* first tree of the random source held (mrpt_build_opts) */
 } mrpt_index_info;
 
 int mrpt_info(const mrpt_index *idx, mrpt_index_info *info);
@@ -310,6 +318,54 @@ int mrpt_export(const mrpt_index *idx, int32_t what, void *dst, int64_t dst_byte
 #define MRPT_NOALLOC_MAX_LEAF_ENTRIES 1048512 /* (4 MiB - 256 B) / 4 */
 int mrpt_query_noalloc(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
                        int32_t n_trees, int32_t *out_ids, float *out_dists);
+
+/*
+ * Tree-sharded voting (Sec. I-C: the trees of an index are independent, so
+ * they can be spread over machines).  Build one index per shard with
+ * mrpt_build_opts.tree_offset (shard g holds trees t_g .. t_g + T_g - 1 of
+ * one seed), count each query's votes among the local trees with
+ * mrpt_vote_counts, exchange the lists (any transport), and answer each
+ * query on the shard that owns it with mrpt_query_from_counts.  F(x;q) is
+ * the sum of the shards' counts and S = {x : F >= v} (Sec. III-A), so the
+ * rows are those of one index that holds all the trees.
+ *
+ * mrpt_vote_counts -- for each of the m queries, every id with at least one
+ * vote among the index's first n_trees trees (0 = all) and its count, ids
+ * ascending.
+ *   Q           m x d float32, device memory.
+ *   cap         row capacity of out_ids and out_counts, at least
+ *               min(n_trees ceil(n / 2^l), n), the most ids a query can meet.
+ *   out_nnz     int32 [m]: ids written for each query.
+ *   out_ids     int32 [m x cap]: row i's first out_nnz[i] entries.
+ *   out_counts  uint8 [m x cap]: their counts (1 .. n_trees).
+ * Every buffer is device memory; stream-ordered on the index's stream.
+ * Errors: INVALID_ARG (cap below the bound, given in the message; a host
+ * buffer), OOM, CUDA.
+ */
+int mrpt_vote_counts(mrpt_index *idx, const float *Q, int64_t m, int32_t n_trees, int64_t cap,
+                     int32_t *out_nnz, int32_t *out_ids, uint8_t *out_counts);
+
+/*
+ * mrpt_query_from_counts -- Algorithm 4 from vote counts gathered from the
+ * shards: query i's (id, count) pairs are entries off[i] .. off[i+1]-1 of
+ * ids and counts, in any order and with an id repeated once per shard.
+ * F(x;q) is the sum of x's counts; it must stay within 255, which holds for
+ * disjoint shards of MRPT_MAX_TREES trees in all.  S = {x : F >= v} and the
+ * rows are those of mrpt_query: the k nearest members of S by (distance,
+ * id), padded with (-1, +inf).  Ids outside [0, n) are ignored.
+ *   Q           m x d float32 queries.
+ *   off         int64 [m+1], non-decreasing from 0.
+ *   v           1 .. MRPT_MAX_TREES.
+ *   opts        NULL or options: precision, margin, chunk and ring as in
+ *               mrpt_query_ex (the other fields are ignored).
+ *   out_ids, out_dists   m x k.
+ * Every buffer is device memory.  The call copies off to the host and waits
+ * for it, then runs stream-ordered on the index's stream.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int mrpt_query_from_counts(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
+                           const int64_t *off, const int32_t *ids, const uint8_t *counts,
+                           const mrpt_query_opts *opts, int32_t *out_ids, float *out_dists);
 
 /* Fault injection for tests: make the allocation after the next `after`
  * successful ones fail with MRPT_ERR_OOM (negative disables).  Host-side

@@ -52,7 +52,7 @@ ABI_SYMBOLS = (
     "mrpt_set_stream", "mrpt_sync", "mrpt_info", "mrpt_export_size", "mrpt_export",
     "mrpt_debug_fail_alloc_after", "mrpt_query_noalloc", "mrpt_add_lowp",
     "mrpt_plan_create", "mrpt_plan_run", "mrpt_plan_free", "mrpt_save", "mrpt_load",
-    "mrpt_build_ex", "mrpt_debug_row_wait_tries",
+    "mrpt_build_ex", "mrpt_debug_row_wait_tries", "mrpt_vote_counts", "mrpt_query_from_counts",
 )
 MRPT_SPARSITY_BERNOULLI = 0
 MRPT_SPARSITY_FIXED = 1
@@ -69,7 +69,7 @@ class MRPTError(RuntimeError):
 
 
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("sparsity", ctypes.c_int32)]
+    _fields_ = [("sparsity", ctypes.c_int32), ("tree_offset", ctypes.c_int32)]
 
 
 class QueryOpts(ctypes.Structure):
@@ -100,6 +100,7 @@ class IndexInfo(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("nnz", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
+        ("tree_offset", ctypes.c_int32),
     ]
 
 
@@ -153,6 +154,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.mrpt_debug_fail_alloc_after.argtypes = [i32]
         lib.mrpt_debug_row_wait_tries.restype = ctypes.c_int
         lib.mrpt_debug_row_wait_tries.argtypes = [i32]
+        lib.mrpt_vote_counts.restype = ctypes.c_int
+        lib.mrpt_vote_counts.argtypes = [vp, vp, i64, i32, i64, vp, vp, vp]
+        lib.mrpt_query_from_counts.restype = ctypes.c_int
+        lib.mrpt_query_from_counts.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, ctypes.POINTER(QueryOpts),
+                                               vp, vp]
         lib.mrpt_plan_create.restype = ctypes.c_int
         lib.mrpt_plan_create.argtypes = [vp, i64, i32, i32, ctypes.POINTER(QueryOpts),
                                          ctypes.POINTER(vp)]
@@ -265,6 +271,7 @@ class Index:
         _check(self._lib.mrpt_info(self._h, ctypes.byref(info)))
         self.n, self.d, self.T, self.l = info.n, info.d, info.T, info.l
         self.density, self.seed, self.nnz = info.density, info.seed, info.nnz
+        self.tree_offset = info.tree_offset
 
     @property
     def handle(self):
@@ -300,18 +307,20 @@ class Index:
 
 
 def mrpt_build(data, T: int, l: int, density: float = 0.0, seed: int = 0,
-               sparsity: int = MRPT_SPARSITY_BERNOULLI) -> Index:
+               sparsity: int = MRPT_SPARSITY_BERNOULLI, tree_offset: int = 0) -> Index:
     """Algorithm 1: grow T trees of depth l over the rows of ``data`` (torch
     tensor on the GPU or the host, or a numpy array).  sparsity selects the
     random vectors' nonzeros (mrpt_build_ex): MRPT_SPARSITY_BERNOULLI or
-    MRPT_SPARSITY_FIXED (exactly ceil(density * d) per vector)."""
+    MRPT_SPARSITY_FIXED (exactly ceil(density * d) per vector).  With
+    ``tree_offset`` t0 the index holds trees t0 .. t0+T-1 of the random
+    source: one shard of a tree-sharded index."""
     lib = load_library()
     data = _as_f32(data)
     if len(data.shape) != 2:
         raise ValueError(f"data must be a 2-D (n, d) matrix, got shape {tuple(data.shape)}")
     n, d = data.shape
     h = ctypes.c_void_p()
-    opts = BuildOpts(int(sparsity))
+    opts = BuildOpts(int(sparsity), int(tree_offset))
     _check(lib.mrpt_build_ex(_ptr(data), n, d, T, l, float(density), seed & (2**64 - 1),
                              ctypes.byref(opts), ctypes.byref(h)))
     if _is_torch(data) and data.is_cuda:
@@ -449,6 +458,68 @@ def mrpt_export(index: Index, what: str) -> np.ndarray:
 
 def mrpt_debug_fail_alloc_after(after: int) -> None:
     _check(load_library().mrpt_debug_fail_alloc_after(int(after)))
+
+
+def vote_count_capacity(index: Index, n_trees: int = 0) -> int:
+    """Row capacity that mrpt_vote_counts needs: min(n_trees ceil(n / 2^l), n)."""
+    T_use = n_trees if n_trees > 0 else index.T
+    leaf = -(-index.n // (1 << index.l))
+    return min(T_use * leaf, index.n)
+
+
+def mrpt_vote_counts(index: Index, Q, n_trees: int = 0):
+    """Per query, the ids with at least one vote among this index's trees and
+    their counts (one shard's part of F(x;q), Sec. III-A).  Q is a CUDA
+    tensor; returns CUDA tensors (nnz [m] int32, ids [m, cap] int32,
+    counts [m, cap] uint8), row i's first nnz[i] entries used."""
+    import torch
+    lib = load_library()
+    m = _check_queries(Q, index)
+    if not (_is_torch(Q) and Q.is_cuda):
+        raise ValueError("mrpt_vote_counts: Q must be a CUDA tensor")
+    cap = max(1, vote_count_capacity(index, n_trees))
+    nnz = torch.empty((m,), dtype=torch.int32, device=Q.device)
+    ids = torch.empty((m, cap), dtype=torch.int32, device=Q.device)
+    counts = torch.empty((m, cap), dtype=torch.uint8, device=Q.device)
+    stream = _current_stream(Q)
+    if stream is not None:
+        _check(lib.mrpt_set_stream(index.handle, stream))
+    _check(lib.mrpt_vote_counts(index.handle, _ptr(Q), m, int(n_trees), cap, _ptr(nnz), _ptr(ids),
+                                _ptr(counts)))
+    return nnz, ids, counts
+
+
+def mrpt_query_from_counts(index: Index, Q, k: int, v: int, off, ids, counts, out_ids=None,
+                           out_dists=None, precision: int = 0, margin: int = 0, chunk: int = 0,
+                           ring: int = 0):
+    """Algorithm 4 from the shards' vote counts: query i's (id, count) pairs
+    are entries off[i]..off[i+1]-1 of ids/counts (CUDA tensors: int64,
+    int32, uint8); F is their sum per id, S = {F >= v}.  Returns the k-NN
+    rows as CUDA tensors."""
+    import torch
+    lib = load_library()
+    m = _check_queries(Q, index)
+    for name, t, dt in (("off", off, torch.int64), ("ids", ids, torch.int32), ("counts", counts, torch.uint8)):
+        if not (_is_torch(t) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    if off.numel() != m + 1 or ids.numel() != counts.numel():
+        raise ValueError("off must hold m + 1 offsets and ids/counts the same number of entries")
+    if out_ids is None:
+        out_ids = torch.empty((m, k), dtype=torch.int32, device=Q.device)
+    if out_dists is None:
+        out_dists = torch.empty((m, k), dtype=torch.float32, device=Q.device)
+    _check_matrix("out_ids", out_ids, m, k, np.int32)
+    _check_matrix("out_dists", out_dists, m, k, np.float32)
+    stream = _current_stream(Q)
+    if stream is not None:
+        _check(lib.mrpt_set_stream(index.handle, stream))
+    opts = QueryOpts()
+    opts.precision, opts.margin, opts.chunk, opts.ring = int(precision), int(margin), int(chunk), int(ring)
+    _check(lib.mrpt_query_from_counts(index.handle, _ptr(Q), m, int(k), int(v), _ptr(off),
+                                      _ptr(ids) if ids.numel() else None,
+                                      _ptr(counts) if counts.numel() else None, ctypes.byref(opts),
+                                      _ptr(out_ids), _ptr(out_dists)))
+    return out_ids, out_dists
 
 
 def mrpt_debug_row_wait_tries(tries: int) -> None:

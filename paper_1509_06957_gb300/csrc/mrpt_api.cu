@@ -150,6 +150,7 @@ static void free_index(mrpt_index *idx) {
     idx->o_stage.release();
     idx->dbg_stage.release();
     idx->q_cand.release();
+    idx->shard.release();
     delete idx;
 }
 
@@ -253,6 +254,11 @@ int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l,
         set_error("mrpt_build: unknown sparsity " + std::to_string(sparsity));
         return MRPT_ERR_INVALID_ARG;
     }
+    const int32_t tree_offset = opts ? opts->tree_offset : 0;
+    if (tree_offset < 0 || int64_t(tree_offset) + T > MRPT_MAX_TREES) {
+        set_error("mrpt_build: need 0 <= tree_offset and tree_offset + T <= " + std::to_string(MRPT_MAX_TREES));
+        return MRPT_ERR_INVALID_ARG;
+    }
     *out = nullptr;
     if (!data || n < 1 || n > int64_t(INT32_MAX) || d < 1 || d > MRPT_MAX_DIM || T < 1 ||
         T > MRPT_MAX_TREES || l < 0 || l > MRPT_MAX_DEPTH || (int64_t(1) << l) > n ||
@@ -280,6 +286,7 @@ int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l,
     idx->L = int64_t(1) << l;
     idx->density = density;
     idx->seed = seed;
+    idx->tree_offset = tree_offset;
     idx->stream = nullptr;
     cudaStream_t s = idx->stream;
 
@@ -308,7 +315,8 @@ int mrpt_build_ex(const float *data, int64_t n, int32_t d, int32_t T, int32_t l,
     }
 
     // ---- random matrix (Algorithm 1, Sec. II-B/II-C)
-    generate_random_matrix(T, l, d, density, seed, sparsity, idx->h_col_off, idx->h_dim, idx->h_val);
+    generate_random_matrix(T, l, d, density, seed, sparsity, tree_offset, idx->h_col_off, idx->h_dim,
+                           idx->h_val);
     idx->nnz = int64_t(idx->h_dim.size());
     const size_t cbytes = idx->h_col_off.size() * sizeof(int32_t);
     const size_t nbytes = size_t(idx->nnz) * sizeof(int32_t);
@@ -398,9 +406,10 @@ int mrpt_info(const mrpt_index *idx, mrpt_index_info *info) {
     info->density = idx->density;
     info->seed = idx->seed;
     info->nnz = idx->nnz;
+    info->tree_offset = idx->tree_offset;
     info->device_bytes = idx->device_bytes + int64_t(idx->q_leaf.bytes + idx->q_stage.bytes +
                                                      idx->o_stage.bytes + idx->dbg_stage.bytes +
-                                                     idx->q_cand.bytes);
+                                                     idx->q_cand.bytes + idx->shard.bytes);
     return MRPT_OK;
 }
 
@@ -784,6 +793,7 @@ struct FileHeader {
     float density;
     uint64_t seed;
     int64_t nnz;
+    int32_t tree_offset, reserved;
 };
 
 int write_all(FILE *f, const void *p, size_t bytes) { return fwrite(p, 1, bytes, f) == bytes ? 0 : -1; }
@@ -803,7 +813,7 @@ int mrpt_save(const mrpt_index *idx, const char *path) {
         return MRPT_ERR_INVALID_ARG;
     }
     FileHeader h{};
-    memcpy(h.magic, "MRPTIDX1", 8);
+    memcpy(h.magic, "MRPTIDX2", 8);
     h.n = idx->n;
     h.d = idx->d;
     h.T = idx->T;
@@ -811,6 +821,7 @@ int mrpt_save(const mrpt_index *idx, const char *path) {
     h.density = idx->density;
     h.seed = idx->seed;
     h.nnz = idx->nnz;
+    h.tree_offset = idx->tree_offset;
     const size_t sb = size_t(idx->T) * size_t(idx->L - 1) * 4;
     const size_t ib = size_t(idx->T) * size_t(idx->n) * 4;
     const size_t xb = size_t(idx->n) * size_t(idx->d) * 4;
@@ -858,9 +869,10 @@ int mrpt_load(const char *path, mrpt_index **out) {
         return MRPT_ERR_INVALID_ARG;
     }
     FileHeader h{};
-    if (read_all(f, &h, sizeof(h)) || memcmp(h.magic, "MRPTIDX1", 8) != 0 || h.n < 1 || h.d < 1 ||
+    if (read_all(f, &h, sizeof(h)) || memcmp(h.magic, "MRPTIDX2", 8) != 0 || h.n < 1 || h.d < 1 ||
         h.d > MRPT_MAX_DIM || h.T < 1 || h.T > MRPT_MAX_TREES || h.l < 0 || h.l > MRPT_MAX_DEPTH ||
-        (int64_t(1) << h.l) > h.n || h.nnz < 0) {
+        (int64_t(1) << h.l) > h.n || h.nnz < 0 || h.tree_offset < 0 ||
+        int64_t(h.tree_offset) + h.T > MRPT_MAX_TREES) {
         fclose(f);
         set_error("mrpt_load: not an index file or unsupported header");
         return MRPT_ERR_INVALID_ARG;
@@ -881,6 +893,7 @@ int mrpt_load(const char *path, mrpt_index **out) {
     idx->density = h.density;
     idx->seed = h.seed;
     idx->nnz = h.nnz;
+    idx->tree_offset = h.tree_offset;
     auto fail = [&](int code, const char *msg) {
         fclose(f);
         if (msg) set_error(msg);

@@ -52,7 +52,7 @@ int32_t fixed_nonzeros(float density, int32_t d) {
 }
 
 void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
-                            int32_t sparsity, std::vector<int32_t> &col_off,
+                            int32_t sparsity, int32_t tree_offset, std::vector<int32_t> &col_off,
                             std::vector<int32_t> &dim, std::vector<float> &val) {
     const double a = double(density);
     const double tau = 2.0 * 3.14159265358979323846;
@@ -73,7 +73,9 @@ void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint
     };
     for (int64_t c = 0; c < ncols; ++c) {
         col_off[size_t(c)] = int32_t(dim.size());
-        const uint64_t base = 3ULL * uint64_t(c) * uint64_t(d);
+        // column c of this index is column tree_offset * l + c of the
+        // random source (tree t of the index is tree tree_offset + t)
+        const uint64_t base = 3ULL * (uint64_t(c) + uint64_t(tree_offset) * uint64_t(l)) * uint64_t(d);
         if (fixed) {
             // the k dimensions with the smallest (first draw, dimension)
             for (int32_t i = 0; i < d; ++i)

@@ -61,6 +61,7 @@ struct mrpt_index {
     float density = 0.f;
     uint64_t seed = 0;
     int64_t nnz = 0;
+    int32_t tree_offset = 0;  // tree t of this index is tree tree_offset + t of the random source
     int device = 0;
     cudaStream_t stream = nullptr;
 
@@ -97,6 +98,7 @@ struct mrpt_index {
     mrpt::Scratch o_stage;   // staged outputs (m x k ids + m x k dists)
     mrpt::Scratch dbg_stage; // staged debug outputs
     mrpt::Scratch q_cand;    // candidate lists, |S| per query, work items, partial lists
+    mrpt::Scratch shard;     // tree-sharded voting: dense vote rows and search scratch
 
     int64_t device_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing (created on first use)
@@ -112,9 +114,10 @@ namespace mrpt {
 
 // Random matrix of Algorithm 1 on the host (counter-based SplitMix64 +
 // Box-Muller); compressed columns, column c = t*l + j.  sparsity is
-// MRPT_SPARSITY_BERNOULLI or MRPT_SPARSITY_FIXED (see mrpt_build_ex).
+// MRPT_SPARSITY_BERNOULLI or MRPT_SPARSITY_FIXED (see mrpt_build_ex); tree t
+// takes the draws of tree tree_offset + t.
 void generate_random_matrix(int32_t T, int32_t l, int32_t d, float density, uint64_t seed,
-                            int32_t sparsity, std::vector<int32_t> &col_off,
+                            int32_t sparsity, int32_t tree_offset, std::vector<int32_t> &col_off,
                             std::vector<int32_t> &dim, std::vector<float> &val);
 
 // Nonzeros per vector of MRPT_SPARSITY_FIXED: ceil(density * d) in [1, d].
@@ -123,6 +126,17 @@ int32_t fixed_nonzeros(float density, int32_t d);
 // Most work items (chunks of its candidate list) that the candidate search
 // makes of one query; long lists get longer chunks.
 constexpr int CAND_ITEMS_MAX = 128;
+
+// Work items of the candidate search for a query with c candidates: chunks
+// of item_size(c) consecutive list entries, at least `chunk` and at most
+// CAND_ITEMS_MAX chunks per query (one item even when S is empty, so that
+// the row gets its padding).  item_count(c) * item_size(c) >= c and every
+// item holds at least one candidate when c > 0.
+__host__ __device__ __forceinline__ int item_size(int c, int chunk) {
+    const int per = (c + CAND_ITEMS_MAX - 1) / CAND_ITEMS_MAX;
+    return chunk > per ? chunk : per;
+}
+__host__ __device__ __forceinline__ int item_count(int c, int csz) { return c == 0 ? 1 : (c + csz - 1) / csz; }
 
 // Ids whose 8-bit vote counters fit in shared memory at once (64 KB).
 constexpr int64_t VOTE_CHUNK_IDS = 65536;
@@ -178,6 +192,8 @@ struct QueryLaunch {
     int32_t *cand;         // optional m x cand_cap
     int64_t cand_cap;
     float *stage_ms;       // optional host float[4]
+    const int64_t *cand_off; // optional: query i's candidate list starts at cand_list + cand_off[i]
+                             // (instead of i * capq)
     int32_t path;          // 0: vote/emit + candidate search, 1: one fused kernel
     int32_t *cand_list;    // m x capq candidate lists (path 0)
     int32_t capq;          // >= |S| of any query: T ceil(n / 2^l) / v, at most n
@@ -202,6 +218,11 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql);
 
 // Routing alone (projection and descent) for ql.m queries into ql.leaf.
 int launch_route_only(mrpt_index *idx, const QueryLaunch &ql);
+
+// The candidate search alone (k_cand_knn): the candidate lists (ql.cand_list
+// with ql.capq or ql.cand_off), |S| (ql.ncand), the work items and their
+// counter (counter word 5) must already be written; counter word 2 must be 0.
+int launch_search_only(mrpt_index *idx, const QueryLaunch &ql);
 
 // launch_query with caller-supplied scratch: ql.leaf holds the m x n_trees
 // leaf-of-query table and `work` the work counter.

@@ -1260,16 +1260,6 @@ struct VoteEmitArgs {
     int32_t sentinel;
 };
 
-// Work items of the candidate search for a query with c candidates: chunks
-// of item_size(c) consecutive list entries, at least `chunk` and at most
-// CAND_ITEMS_MAX chunks per query (one item even when S is empty, so that
-// the row gets its padding).  item_count(c) * item_size(c) >= c and every
-// item holds at least one candidate when c > 0.
-__device__ __forceinline__ int item_size(int c, int chunk) {
-    return max(chunk, (c + CAND_ITEMS_MAX - 1) / CAND_ITEMS_MAX);
-}
-__device__ __forceinline__ int item_count(int c, int csz) { return c == 0 ? 1 : (c + csz - 1) / csz; }
-
 // Called by one thread once a query's votes are all in: records |S| and
 // appends the query's work items.  capq bounds |S| (|S| <= T ceil(n / 2^l) / v,
 // Sec. III-B), so the list always held every candidate.
@@ -1849,7 +1839,14 @@ struct CandKnnArgs {
     const QueryRecord *rec;  // plan mode: Q, outputs and m of the batch
     uint32_t wait_tries;   // tries of each row wait of the distance loop (a test
                            // shortens it so that the wait runs out)
+    const int64_t *cand_off;  // optional: query i's list starts at cand + cand_off[i]
 };
+
+// First candidate of query qi's list: lists of capq entries one after
+// another, or at per-query offsets.
+__device__ __forceinline__ const int32_t *cand_list_of(const CandKnnArgs &a, int64_t qi) {
+    return a.cand + (a.cand_off != nullptr ? a.cand_off[qi] : qi * int64_t(a.capq));
+}
 
 template <int KR>
 __global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs a0) {
@@ -1878,7 +1875,7 @@ __global__ void __launch_bounds__(CK_THREADS) k_cand_knn_regs(const CandKnnArgs 
         __syncwarp();
         WarpTopK<KR> top;
         top.init();
-        const int32_t *clist = a.cand + qi * int64_t(a.capq);
+        const int32_t *clist = cand_list_of(a, qi);
         for (int base = 0; base < c; base += 32) {
             const int32_t mine = (base + lane < c) ? __ldg(clist + base + lane) : 0;
             const int cb = min(32, c - base);
@@ -1991,7 +1988,7 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
             }
             staged_q = qi;
         }
-        const int32_t *clist = a.cand + qi * int64_t(a.capq) + lo;
+        const int32_t *clist = cand_list_of(a, qi) + lo;
         // candidate ids f in [cbase, cbase + 64) in the warp's shared list
         // (f stays below j + 1 + S < cbase + 32 + 17)
         int32_t *cid = s_cid[warp];
@@ -2476,6 +2473,7 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.part_d = ql.part_d;
     a.part_i = ql.part_i;
     a.wait_tries = debug_row_wait_tries();
+    a.cand_off = ql.cand_off;
     int sms = 0, per_sm = 0;
     cudaError_t e;
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
@@ -2500,7 +2498,39 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     return cudaGetLastError();
 }
 
+// k_cand_knn for ql's precision and k (the candidate lists, |S| and work
+// items already written).
+cudaError_t launch_search_any(const mrpt_index *idx, const QueryLaunch &ql, cudaStream_t s) {
+    const int kr = (ql.k + 31) / 32;
+    if (ql.precision == 1) {
+        // survivors kept for the re-rank (none beyond k when it is skipped)
+        const int krs = (ql.k + (idx->bf16_exact ? 0 : ql.margin) + 31) / 32;
+        if (krs <= 1) return launch_cand_knn<1, 1>(idx, ql, s);
+        if (krs <= 2) return launch_cand_knn<2, 1>(idx, ql, s);
+        if (krs <= 4) return launch_cand_knn<4, 1>(idx, ql, s);
+        return launch_cand_knn<8, 1>(idx, ql, s);
+    }
+    if (ql.precision == 2) {
+        const int krs = (ql.k + ql.margin + 31) / 32;
+        if (krs <= 1) return launch_cand_knn<1, 2>(idx, ql, s);
+        if (krs <= 2) return launch_cand_knn<2, 2>(idx, ql, s);
+        if (krs <= 4) return launch_cand_knn<4, 2>(idx, ql, s);
+        return launch_cand_knn<8, 2>(idx, ql, s);
+    }
+    if (kr <= 1) return launch_cand_knn<1, 0>(idx, ql, s);
+    if (kr <= 2) return launch_cand_knn<2, 0>(idx, ql, s);
+    if (kr <= 4) return launch_cand_knn<4, 0>(idx, ql, s);
+    return launch_cand_knn<8, 0>(idx, ql, s);
+}
+
 }  // namespace
+
+int launch_search_only(mrpt_index *idx, const QueryLaunch &ql) {
+    if (ql.m == 0) return MRPT_OK;
+    const cudaError_t e = launch_search_any(idx, ql, ql.use_stream ? ql.stream : idx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
+    return MRPT_OK;
+}
 
 int launch_route_only(mrpt_index *idx, const QueryLaunch &ql) {
     if (ql.m == 0) return MRPT_OK;
@@ -2544,36 +2574,7 @@ int launch_query(mrpt_index *idx, const QueryLaunch &ql) {
         e = launch_vote_emit(idx, ql, s);
         if (e != cudaSuccess) return cuda_fail(e, "k_vote_emit");
         if (ql.stage_ms) MRPT_CUDA_TRY(cudaEventRecord(idx->ev[2], s));
-        if (ql.precision == 1) {
-            // survivors kept for the re-rank (none beyond k when it is skipped)
-            const int krs = (ql.k + (idx->bf16_exact ? 0 : ql.margin) + 31) / 32;
-            if (krs <= 1)
-                e = launch_cand_knn<1, 1>(idx, ql, s);
-            else if (krs <= 2)
-                e = launch_cand_knn<2, 1>(idx, ql, s);
-            else if (krs <= 4)
-                e = launch_cand_knn<4, 1>(idx, ql, s);
-            else
-                e = launch_cand_knn<8, 1>(idx, ql, s);
-        } else if (ql.precision == 2) {
-            const int krs = (ql.k + ql.margin + 31) / 32;
-            if (krs <= 1)
-                e = launch_cand_knn<1, 2>(idx, ql, s);
-            else if (krs <= 2)
-                e = launch_cand_knn<2, 2>(idx, ql, s);
-            else if (krs <= 4)
-                e = launch_cand_knn<4, 2>(idx, ql, s);
-            else
-                e = launch_cand_knn<8, 2>(idx, ql, s);
-        } else if (kr <= 1) {
-            e = launch_cand_knn<1, 0>(idx, ql, s);
-        } else if (kr <= 2) {
-            e = launch_cand_knn<2, 0>(idx, ql, s);
-        } else if (kr <= 4) {
-            e = launch_cand_knn<4, 0>(idx, ql, s);
-        } else {
-            e = launch_cand_knn<8, 0>(idx, ql, s);
-        }
+        e = launch_search_any(idx, ql, s);
         if (e != cudaSuccess) return cuda_fail(e, "k_cand_knn");
     }
     if (ql.stage_ms) {
