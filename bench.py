@@ -170,16 +170,17 @@ def kernel_source_sha(kernel: str, path: str) -> str:
     return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
 
 
-def load_traffic(kernel: str, src: str):
-    """DRAM bytes per launch from the committed ncu summary of `kernel`, if
-    it was taken on the kernel's current source (else None)."""
+def load_traffic(kernel: str, src: str, key: str = "dram_bytes_per_launch"):
+    """A figure (DRAM bytes per launch by default) from the committed ncu
+    summary of `kernel`, if it was taken on the kernel's current source
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     entry = json.load(open(p)).get(kernel)
     if not entry or entry.get("source_sha") != kernel_source_sha(kernel, src):
         return None
-    return entry.get("dram_bytes_per_launch")
+    return entry.get(key)
 
 
 # ------------------------------------------------------- ground truth -----
@@ -358,6 +359,7 @@ def run_gpu(args):
         achieved = per_query * m / (ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": load_traffic(name, src),
+                "l2_sectors_pct": load_traffic(name, src, "l2_sectors_pct_of_peak"),
                 "peak_kind": f"{peak_kind} hbm_gbs", "kernel": name,
                 "bytes_per_query": round(per_query, 1), "avg_ms": round(ms, 4)}
 
