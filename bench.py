@@ -779,7 +779,7 @@ def run_pareto(args):
     """--workload pareto: the paper's parameter search (Sec. IV-B: grid over
     T, depth and v with a = 1/sqrt(d)) as Pareto fronts of queries/s against
     recall@k for k in {1, 10, 100}, for MRPT and the ablations of Table III:
-    fixed-count sparse vectors (exactly ceil(a d) nonzeros, the Sec. II-B
+    fixed-count sparse vectors (exactly ceil(a d) nonzeros, the Sec. II-D
     footnote), sparse trees without voting (v = 1), and classic dense RP
     trees (a = 1, v = 1).  Also MRPT on the "Random" set (unit-length
     N(0, I), 50,000 x 4096, Sec. IV-A).  Time is the library's device time of

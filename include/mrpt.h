@@ -96,7 +96,7 @@ int mrpt_build(const float *data, int64_t n, int32_t d, int32_t T, int32_t l, fl
  *     MRPT_SPARSITY_FIXED (1): exactly ceil(density * d) nonzeros per vector
  *       (at least 1, at most d; density * d is taken with a relative
  *       allowance of 1e-6, since density is a float) -- the variant in the
- *       footnote of Sec. II-B, an ablation of Table III.  The nonzero
+ *       footnote of Sec. II-D, an ablation of Table III.  The nonzero
  *       dimensions are those with the smallest (first draw, dimension), the
  *       first draw being the one the Bernoulli rule compares with density,
  *       so the set is a uniformly random subset; values are the same N(0,1)

@@ -158,7 +158,7 @@ class RandomMatrix:
 
 
 SPARSITY_BERNOULLI = 0  # each component nonzero with probability a (Sec. II-B)
-SPARSITY_FIXED = 1      # exactly ceil(a d) nonzeros per vector (Sec. II-B footnote)
+SPARSITY_FIXED = 1      # exactly ceil(a d) nonzeros per vector (Sec. II-D footnote)
 
 
 def fixed_count(density: float, d: int) -> int:
@@ -169,7 +169,7 @@ def fixed_count(density: float, d: int) -> int:
 def random_matrix(T: int, l: int, d: int, density: float, seed: int,
                   sparsity: int = SPARSITY_BERNOULLI) -> RandomMatrix:
     """Sparse random vectors of Algorithm 1 (Sec. II-B, II-C); with
-    sparsity=SPARSITY_FIXED, the footnote's variant of Sec. II-B."""
+    sparsity=SPARSITY_FIXED, the variant in the footnote of Sec. II-D."""
     lib = _load()
     fn = lib.orc_random_matrix_fixed if sparsity == SPARSITY_FIXED else lib.orc_random_matrix
     col_off = np.zeros(T * l + 1, dtype=np.int32)

@@ -11,7 +11,7 @@
  *   - orc_random_matrix : Algorithm 1, inner two loops; Sec. II-B (sparse
  *                         vectors r_i ~ N(0,1) w.p. a, else 0); Sec. II-C (one
  *                         vector per tree level, R in R^{d x l}).
- *   - orc_random_matrix_fixed : the footnote of Sec. II-B (exactly ceil(a d)
+ *   - orc_random_matrix_fixed : the footnote of Sec. II-D (exactly ceil(a d)
  *                         nonzeros per vector), the ablation of Table III.
  *   - orc_project       : Algorithm 1 (P = XR) and Algorithm 3 (p = q^T R).
  *   - orc_grow_tree     : Algorithm 2 with the order-based median of Sec. II-A
@@ -134,7 +134,7 @@ static int cmp_i32(const void *pa, const void *pb)
 }
 
 /*
- * The ablation in the footnote of Sec. II-B: every vector has exactly
+ * The ablation in the footnote of Sec. II-D: every vector has exactly
  * k = orc_fixed_count(density, d) nonzeros instead of a Bernoulli(a) draw per
  * component.  Reading: column c's nonzero dimensions are the k dimensions
  * with the smallest (z_i, i), where z_i is the same uniform draw (counter

@@ -1,7 +1,7 @@
 """GPU: index save/load, the paper's fully specified "Random" workload
 (unit-length N(0, I) vectors, d = 4096, Sec. IV-A), the dense (a = 1,
 classic RP tree) ablation and the fixed-count sparse vectors of the
-Sec. II-B footnote, each against the oracle."""
+Sec. II-D footnote, each against the oracle."""
 import os
 
 import numpy as np

@@ -70,7 +70,7 @@ def test_random_matrix_prefix_stable_in_T():
 
 
 def test_fixed_count_variant_counts():
-    """Footnote of Sec. II-B: exactly ceil(a d) nonzeros per vector (at
+    """Footnote of Sec. II-D: exactly ceil(a d) nonzeros per vector (at
     least 1, at most d); values worked by hand."""
     for (a, d, k) in [(1.0 / math.sqrt(784), 784, 28), (0.3, 50, 15), (0.01, 50, 1),
                       (1.0, 50, 50), (1.0 / math.sqrt(128), 128, 12), (0.125, 64, 8)]:
