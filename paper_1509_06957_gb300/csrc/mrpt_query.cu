@@ -2192,6 +2192,254 @@ __global__ void __launch_bounds__(CR_WARPS * 32) k_cand_knn(const CandKnnArgs a0
     }
 }
 
+// --------------------------------------- candidate search, rows in registers
+
+// acc + (x - q)^2 for the 8 bfloat16 values of one 16-byte chunk x against 8
+// float32 query values, two components per packed fma.  Each difference is
+// one mixed-precision subtraction (sub.rn.f32.bf16: the bfloat16 operand is
+// widened exactly, then one rounding), so (x - q)^2 equals the square of the
+// float32 difference q - x of the staged-row kernels.
+__device__ __forceinline__ float2 bf16x8_sq_acc(uint4 x, const float (&q)[8], float2 acc) {
+    float t0, t1, t2, t3, t4, t5, t6, t7;
+    asm("{\n\t"
+        ".reg .b16 h<8>;\n\t"
+        "mov.b32 {h0, h1}, %8;\n\t"
+        "mov.b32 {h2, h3}, %9;\n\t"
+        "mov.b32 {h4, h5}, %10;\n\t"
+        "mov.b32 {h6, h7}, %11;\n\t"
+        "sub.rn.f32.bf16 %0, h0, %12;\n\t"
+        "sub.rn.f32.bf16 %1, h1, %13;\n\t"
+        "sub.rn.f32.bf16 %2, h2, %14;\n\t"
+        "sub.rn.f32.bf16 %3, h3, %15;\n\t"
+        "sub.rn.f32.bf16 %4, h4, %16;\n\t"
+        "sub.rn.f32.bf16 %5, h5, %17;\n\t"
+        "sub.rn.f32.bf16 %6, h6, %18;\n\t"
+        "sub.rn.f32.bf16 %7, h7, %19;\n\t"
+        "}"
+        : "=f"(t0), "=f"(t1), "=f"(t2), "=f"(t3), "=f"(t4), "=f"(t5), "=f"(t6), "=f"(t7)
+        : "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w), "f"(q[0]), "f"(q[1]), "f"(q[2]), "f"(q[3]), "f"(q[4]),
+          "f"(q[5]), "f"(q[6]), "f"(q[7]));
+    acc = __ffma2_rn(make_float2(t0, t1), make_float2(t0, t1), acc);
+    acc = __ffma2_rn(make_float2(t2, t3), make_float2(t2, t3), acc);
+    acc = __ffma2_rn(make_float2(t4, t5), make_float2(t4, t5), acc);
+    acc = __ffma2_rn(make_float2(t6, t7), make_float2(t6, t7), acc);
+    return acc;
+}
+
+// Sums of two per-lane values over the warp, returned in every lane: lanes
+// 0-15 reduce the first and lanes 16-31 the second after one exchange
+// (5 shuffles for both instead of 10).
+__device__ __forceinline__ void warp_sum2(float s0, float s1, int lane, float &d0, float &d1) {
+    const bool hi = (lane & 16) != 0;
+    float mine = hi ? s1 : s0;
+    const float other = hi ? s0 : s1;
+    mine += __shfl_xor_sync(0xffffffffu, other, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    d0 = __shfl_sync(0xffffffffu, mine, 0);
+    d1 = __shfl_sync(0xffffffffu, mine, 16);
+}
+
+// k_cand_knn for a lossless bfloat16 copy (no re-rank) with 32 U >= dpad / 8
+// >= 32 (U - 1): one warp per (query, chunk of the list) work item, as in
+// k_cand_knn, with the rows in a per-warp ring of CB_SLOTS row pairs in
+// shared memory.  Lane l owns the 16-byte chunks l, l + 32, ... (8 values
+// each) of every row: it copies its own chunks of each row into the ring
+// with cp.async and later reads back only what it copied, so a per-thread
+// wait_group is all the synchronisation (no mbarrier, no single lane
+// issuing copies for the warp).  The query's chunks stay in registers for
+// the whole item.  Pairs are copied CB_SLOTS - 1 ahead; each pair's two
+// sums are reduced together and go into the warp's sorted top-k.
+constexpr int CB_WARPS = 4;
+constexpr int CB_SLOTS = 2;
+
+template <int KR, int U>
+__global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnArgs a0) {
+    CandKnnArgs a = a0;
+    if (a.rec != nullptr) {
+        a.Q = a.rec->Q;
+        a.out_ids = a.rec->out_ids;
+        a.out_dists = a.rec->out_dists;
+        a.m = a.rec->m;
+    }
+    extern __shared__ __align__(16) unsigned char cbsm[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nchunk = a.dpad >> 3;  // 16-byte chunks per bfloat16 row
+    const uint4 *Xb = reinterpret_cast<const uint4 *>(a.rows);
+    uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * (CB_SLOTS * 2) * nchunk;
+    const uint32_t wring_s = smem_u32(wring);
+    const int k = a.k;
+    const uint32_t n_items = *a.n_items;
+    const bool qvec = (a.d & 7) == 0 && (reinterpret_cast<uintptr_t>(a.Q) & 15) == 0;
+    float qv[U][8];
+    int64_t staged_q = -1;
+    uint32_t w = 0;
+    if (lane == 0) w = atomicAdd(a.work, 1u);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    int2 item = make_int2(0, 0);
+    int call = 0;
+    if (w < n_items) {
+        item = a.items[w];
+        call = min(a.ncand[item.x], a.capq);
+    }
+    while (w < n_items) {
+        const int64_t qi = item.x;
+        const int ch = item.y;
+        uint32_t w_next = 0;
+        if (lane == 0) w_next = atomicAdd(a.work, 1u);
+        const int csz = item_size(call, a.chunk);
+        const int nch = item_count(call, csz);
+        const int lo = ch * csz;
+        const int c = min(call, lo + csz) - lo;  // candidates of this item
+        if (qi != staged_q) {
+            const float *qrow = a.Q + qi * a.d;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int cc = lane + 32 * u;
+                if (qvec && cc < nchunk && cc * 8 < a.d) {
+                    const float4 x0 = __ldg(reinterpret_cast<const float4 *>(qrow + cc * 8));
+                    const float4 x1 = __ldg(reinterpret_cast<const float4 *>(qrow + cc * 8 + 4));
+                    qv[u][0] = x0.x; qv[u][1] = x0.y; qv[u][2] = x0.z; qv[u][3] = x0.w;
+                    qv[u][4] = x1.x; qv[u][5] = x1.y; qv[u][6] = x1.z; qv[u][7] = x1.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int dim = cc * 8 + e;
+                        qv[u][e] = (cc < nchunk && dim < a.d) ? __ldg(qrow + dim) : 0.f;
+                    }
+                }
+            }
+            staged_q = qi;
+        }
+        const int32_t *clist = cand_list_of(a, qi) + lo;
+        // ids of rows [32 blk, 32 blk + 32) of the item, one per lane
+        int blk = 0;
+        int32_t ids = lane < c ? __ldg(clist + lane) : 0;
+        auto id_of = [&](int r) -> int32_t {
+            if ((r >> 5) != blk) {
+                blk = r >> 5;
+                const int rr = 32 * blk + lane;
+                ids = rr < c ? __ldg(clist + rr) : 0;
+            }
+            return __shfl_sync(0xffffffffu, ids, r & 31);
+        };
+        // copy pair p (rows 2p and 2p + 1; an odd item's last row twice) into
+        // slot p % CB_SLOTS, one commit group per pair (empty past the item's
+        // last pair).  Rounds u < U - 1 are always inside the row
+        // (32 (U - 1) < dpad / 8), only the last one needs a bound.
+        auto issue_pair = [&](int p, int slot) {
+            if (2 * p < c) {
+                const int32_t id0 = id_of(2 * p);
+                const int32_t id1 = 2 * p + 1 < c ? id_of(2 * p + 1) : id0;
+                const uint4 *s0 = Xb + int64_t(id0) * nchunk + lane;
+                const uint4 *s1 = Xb + int64_t(id1) * nchunk + lane;
+                const uint32_t d0 = wring_s + uint32_t(slot * 2 * nchunk + lane) * 16u;
+                const uint32_t d1 = d0 + uint32_t(nchunk) * 16u;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (u < U - 1 || lane + 32 * u < nchunk) {
+                        cp_async16_zfill(d0 + uint32_t(32 * u) * 16u, s0 + 32 * u, 16u);
+                        cp_async16_zfill(d1 + uint32_t(32 * u) * 16u, s1 + 32 * u, 16u);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        WarpTopK<KR> top;
+        top.init();
+        const int npairs = (c + 1) >> 1;
+        int s_issue = 0, s_use = 0;  // slots of the next pair to copy and to use
+#pragma unroll
+        for (int p = 0; p < CB_SLOTS - 1; ++p) {
+            issue_pair(p, s_issue);
+            s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
+        }
+        for (int p = 0; p < npairs; ++p) {
+            issue_pair(p + CB_SLOTS - 1, s_issue);
+            s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
+            // this thread's copies of pair p are in (groups of later pairs may not be)
+            asm volatile("cp.async.wait_group %0;" ::"n"(CB_SLOTS - 1) : "memory");
+            const uint4 *r0 = wring + (s_use * 2) * nchunk + lane;
+            const uint4 *r1 = r0 + nchunk;
+            s_use = s_use + 1 == CB_SLOTS ? 0 : s_use + 1;
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = u < U - 1 || lane + 32 * u < nchunk;
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                const uint4 x0 = in ? r0[32 * u] : z;
+                const uint4 x1 = in ? r1[32 * u] : z;
+                a0 = bf16x8_sq_acc(x0, qv[u], a0);
+                a1 = bf16x8_sq_acc(x1, qv[u], a1);
+            }
+            float d0, d1;
+            warp_sum2(a0.x + a0.y, a1.x + a1.y, lane, d0, d1);
+            top.insert(d0, id_of(2 * p), k, lane);
+            if (2 * p + 1 < c) top.insert(d1, id_of(2 * p + 1), k, lane);
+        }
+        cp_async_wait_all();  // no copy of this item outlives it
+        bool finish = nch == 1;
+        if (!finish) {
+            // publish this chunk's list; the item that completes the query
+            // merges every chunk's list into its own
+            const int64_t pbase = (qi * a.max_items_q + ch) * int64_t(k);
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int e = r * 32 + lane;
+                if (e < k) {
+                    a.part_d[pbase + e] = top.d[r];
+                    a.part_i[pbase + e] = top.i[r];
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(a.done + qi, 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            finish = old == nch - 1;
+            if (finish) {
+                __threadfence();
+                for (int ch2 = 0; ch2 < nch; ++ch2) {
+                    if (ch2 == ch) continue;
+                    const int64_t b2 = (qi * a.max_items_q + ch2) * int64_t(k);
+                    for (int e0 = 0; e0 < k; e0 += 32) {
+                        float pd = INFINITY;
+                        int32_t pi = SENTINEL_ID;
+                        if (e0 + lane < k) {
+                            pd = __ldcg(a.part_d + b2 + e0 + lane);
+                            pi = __ldcg(a.part_i + b2 + e0 + lane);
+                        }
+                        const int cnt = min(32, k - e0);
+                        for (int u = 0; u < cnt; ++u) {
+                            const float ud = __shfl_sync(0xffffffffu, pd, u);
+                            const int32_t ui = __shfl_sync(0xffffffffu, pi, u);
+                            top.insert(ud, ui, k, lane);
+                        }
+                    }
+                }
+            }
+        }
+        if (finish) {
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const int e = r * 32 + lane;
+                if (e < k) {
+                    const bool real = top.i[r] != SENTINEL_ID;
+                    a.out_ids[qi * k + e] = real ? top.i[r] : -1;
+                    a.out_dists[qi * k + e] = real ? sqrtf(top.d[r]) : INFINITY;
+                }
+            }
+        }
+        __syncwarp();
+        w = __shfl_sync(0xffffffffu, w_next, 0);
+        if (w < n_items) {
+            item = a.items[w];
+            call = min(a.ncand[item.x], a.capq);
+        }
+    }
+}
+
 // -------------------------------------------------------------- launch ----
 
 namespace {
@@ -2476,6 +2724,22 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.cand_off = ql.cand_off;
     int sms = 0, per_sm = 0;
     cudaError_t e;
+    // a lossless bfloat16 copy of 256 <= dpad <= 1024: rows straight into registers
+    const int nchunk = idx->dpad / 8;
+    if (RK == 1 && !rerank && nchunk >= 32 && nchunk <= 128) {
+        const int U = (nchunk + 31) / 32;
+        auto kern = U == 1 ? k_cand_knn_bf16<KR, 1>
+                    : U == 2 ? k_cand_knn_bf16<KR, 2>
+                    : U == 3 ? k_cand_knn_bf16<KR, 3>
+                             : k_cand_knn_bf16<KR, 4>;
+        const size_t smem = size_t(CB_WARPS) * CB_SLOTS * 2 * size_t(nchunk) * 16;
+        e = launch_shape(reinterpret_cast<const void *>(kern), CB_WARPS * 32, smem, idx->device, &per_sm, &sms);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::max<int64_t>(
+            1, std::min<int64_t>((ql.m * 4 + CB_WARPS - 1) / CB_WARPS, int64_t(sms) * std::max(per_sm, 1)));
+        kern<<<unsigned(blocks), CB_WARPS * 32, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
         // the default two-slot ring of k <= 64 as a compile-time constant
