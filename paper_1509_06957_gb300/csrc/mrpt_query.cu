@@ -2240,21 +2240,40 @@ __device__ __forceinline__ void warp_sum2(float s0, float s1, int lane, float &d
     d1 = __shfl_sync(0xffffffffu, mine, 16);
 }
 
-// k_cand_knn for a lossless bfloat16 copy (no re-rank) with 32 U >= dpad / 8
-// >= 32 (U - 1): one warp per (query, chunk of the list) work item, as in
-// k_cand_knn, with the rows in a per-warp ring of CB_SLOTS row pairs in
-// shared memory.  Lane l owns the 16-byte chunks l, l + 32, ... (8 values
-// each) of every row: it copies its own chunks of each row into the ring
-// with cp.async and later reads back only what it copied, so a per-thread
-// wait_group is all the synchronisation (no mbarrier, no single lane
-// issuing copies for the warp).  The query's chunks stay in registers for
-// the whole item.  Pairs are copied CB_SLOTS - 1 ahead; each pair's two
-// sums are reduced together and go into the warp's sorted top-k.
+// The same for the 4 float32 values of one 16-byte chunk of a float32 row.
+__device__ __forceinline__ float2 f32x4_sq_acc(uint4 x, const float *q, float2 acc) {
+    acc = sq_acc2(make_float2(q[0], q[1]), make_float2(__uint_as_float(x.x), __uint_as_float(x.y)), acc);
+    return sq_acc2(make_float2(q[2], q[3]), make_float2(__uint_as_float(x.z), __uint_as_float(x.w)), acc);
+}
+__device__ __forceinline__ float2 chunk_sq_acc(uint4 x, const float (&q)[8], float2 acc) {
+    return bf16x8_sq_acc(x, q, acc);
+}
+__device__ __forceinline__ float2 chunk_sq_acc(uint4 x, const float (&q)[4], float2 acc) {
+    return f32x4_sq_acc(x, q, acc);
+}
+
+// k_cand_knn for float32 rows (RT = 0) or bfloat16 rows (RT = 1) whose
+// 16-byte chunks (4 or 8 values) number between 32 (U - 1) + 1 and 32 U:
+// one warp per (query, chunk of the list) work item, as in k_cand_knn, with
+// the rows in a per-warp ring of CB_SLOTS row pairs in shared memory.
+// - Lane l owns chunks l, l + 32, ... of every row. It copies its own chunks
+//   of each row into the ring with cp.async and later reads back only what it
+//   copied. A per-thread wait_group is therefore all the synchronisation: no
+//   mbarrier, and no single lane issuing copies for the warp.
+// - The query's chunks stay in registers for the whole item.
+// - Pairs are copied CB_SLOTS - 1 ahead. Each pair's two sums are reduced
+//   together and go into the warp's sorted top-k.
+// - With a lossy bfloat16 copy the item that completes a query re-ranks the
+//   k + margin survivors with float32 rows. Each survivor's row goes through
+//   the same ring, one row per slot. Lane l copies the two float32 chunks that
+//   cover its bfloat16 chunk's 8 values, so the query registers serve as they
+//   are.
 constexpr int CB_WARPS = 4;
 constexpr int CB_SLOTS = 2;
 
-template <int KR, int U>
-__global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnArgs a0) {
+template <int KR, int U, int RT, bool RR>
+__global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnArgs a0) {
+    constexpr int VPC = RT == 1 ? 8 : 4;  // values per 16-byte chunk
     CandKnnArgs a = a0;
     if (a.rec != nullptr) {
         a.Q = a.rec->Q;
@@ -2265,14 +2284,14 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnAr
     extern __shared__ __align__(16) unsigned char cbsm[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int nchunk = a.dpad >> 3;  // 16-byte chunks per bfloat16 row
+    const int nchunk = a.dpad / VPC;  // 16-byte chunks per row
     const uint4 *Xb = reinterpret_cast<const uint4 *>(a.rows);
     uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * (CB_SLOTS * 2) * nchunk;
     const uint32_t wring_s = smem_u32(wring);
-    const int k = a.k;
+    const int k = a.k;  // survivors kept (k + margin when re-ranking)
     const uint32_t n_items = *a.n_items;
-    const bool qvec = (a.d & 7) == 0 && (reinterpret_cast<uintptr_t>(a.Q) & 15) == 0;
-    float qv[U][8];
+    const bool qvec = (a.d % VPC) == 0 && (reinterpret_cast<uintptr_t>(a.Q) & 15) == 0;
+    float qv[U][VPC];
     int64_t staged_q = -1;
     uint32_t w = 0;
     if (lane == 0) w = atomicAdd(a.work, 1u);
@@ -2297,15 +2316,19 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnAr
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int cc = lane + 32 * u;
-                if (qvec && cc < nchunk && cc * 8 < a.d) {
-                    const float4 x0 = __ldg(reinterpret_cast<const float4 *>(qrow + cc * 8));
-                    const float4 x1 = __ldg(reinterpret_cast<const float4 *>(qrow + cc * 8 + 4));
-                    qv[u][0] = x0.x; qv[u][1] = x0.y; qv[u][2] = x0.z; qv[u][3] = x0.w;
-                    qv[u][4] = x1.x; qv[u][5] = x1.y; qv[u][6] = x1.z; qv[u][7] = x1.w;
+                if (qvec && cc < nchunk && cc * VPC < a.d) {
+#pragma unroll
+                    for (int h = 0; h < VPC / 4; ++h) {
+                        const float4 x = __ldg(reinterpret_cast<const float4 *>(qrow + cc * VPC + 4 * h));
+                        qv[u][4 * h] = x.x;
+                        qv[u][4 * h + 1] = x.y;
+                        qv[u][4 * h + 2] = x.z;
+                        qv[u][4 * h + 3] = x.w;
+                    }
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int dim = cc * 8 + e;
+                    for (int e = 0; e < VPC; ++e) {
+                        const int dim = cc * VPC + e;
                         qv[u][e] = (cc < nchunk && dim < a.d) ? __ldg(qrow + dim) : 0.f;
                     }
                 }
@@ -2370,8 +2393,8 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnAr
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 const uint4 x0 = in ? r0[32 * u] : z;
                 const uint4 x1 = in ? r1[32 * u] : z;
-                a0 = bf16x8_sq_acc(x0, qv[u], a0);
-                a1 = bf16x8_sq_acc(x1, qv[u], a1);
+                a0 = chunk_sq_acc(x0, qv[u], a0);
+                a1 = chunk_sq_acc(x1, qv[u], a1);
             }
             float d0, d1;
             warp_sum2(a0.x + a0.y, a1.x + a1.y, lane, d0, d1);
@@ -2420,14 +2443,69 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_bf16(const CandKnnAr
                 }
             }
         }
+        if (RT == 1 && RR && finish) {
+            // re-rank: exact float32 distances of the k + margin survivors,
+            // one float32 row per ring slot, the next row copied while this
+            // one is summed; keep the kfinal smallest
+            const uint4 *Xf = reinterpret_cast<const uint4 *>(a.X);  // 2 nchunk chunks per row
+            auto sid = [&](int f) -> int32_t {
+                int32_t v = SENTINEL_ID;
+#pragma unroll
+                for (int rr = 0; rr < KR; ++rr) {
+                    const int32_t t2 = __shfl_sync(0xffffffffu, top.i[rr], f & 31);
+                    if (rr == (f >> 5)) v = t2;
+                }
+                return v;
+            };
+            int nsurv = 0;
+#pragma unroll
+            for (int rr = 0; rr < KR; ++rr)
+                nsurv += __popc(__ballot_sync(0xffffffffu, rr * 32 + lane < k && top.i[rr] != SENTINEL_ID));
+            auto issue_row = [&](int f) {
+                if (f < nsurv) {
+                    const uint4 *src = Xf + int64_t(sid(f)) * (2 * nchunk) + 2 * lane;
+                    const uint32_t dst = wring_s + uint32_t((f & 1) * 2 * nchunk + 2 * lane) * 16u;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (u < U - 1 || lane + 32 * u < nchunk) {
+                            cp_async16_zfill(dst + uint32_t(64 * u) * 16u, src + 64 * u, 16u);
+                            cp_async16_zfill(dst + uint32_t(64 * u + 1) * 16u, src + 64 * u + 1, 16u);
+                        }
+                    }
+                }
+                cp_async_commit();
+            };
+            WarpTopK<KR> fin;
+            fin.init();
+            issue_row(0);
+            for (int f = 0; f < nsurv; ++f) {
+                issue_row(f + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                const uint4 *row = wring + (f & 1) * 2 * nchunk + 2 * lane;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (u < U - 1 || lane + 32 * u < nchunk) {
+                        acc = f32x4_sq_acc(row[64 * u], qv[u], acc);
+                        acc = f32x4_sq_acc(row[64 * u + 1], qv[u] + 4, acc);
+                    }
+                }
+                float e0, e1;
+                warp_sum2(acc.x + acc.y, 0.f, lane, e0, e1);
+                fin.insert(e0, sid(f), a.kfinal, lane);
+            }
+            cp_async_wait_all();
+            top = fin;
+        }
         if (finish) {
+            const int kf = a.kfinal;
 #pragma unroll
             for (int r = 0; r < KR; ++r) {
                 const int e = r * 32 + lane;
-                if (e < k) {
+                if (e < kf) {
                     const bool real = top.i[r] != SENTINEL_ID;
-                    a.out_ids[qi * k + e] = real ? top.i[r] : -1;
-                    a.out_dists[qi * k + e] = real ? sqrtf(top.d[r]) : INFINITY;
+                    a.out_ids[qi * kf + e] = real ? top.i[r] : -1;
+                    a.out_dists[qi * kf + e] = real ? sqrtf(top.d[r]) : INFINITY;
                 }
             }
         }
@@ -2724,21 +2802,42 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.cand_off = ql.cand_off;
     int sms = 0, per_sm = 0;
     cudaError_t e;
-    // a lossless bfloat16 copy of 256 <= dpad <= 1024: rows straight into registers
-    const int nchunk = idx->dpad / 8;
-    if (RK == 1 && !rerank && nchunk >= 32 && nchunk <= 128) {
+    // float32 or bfloat16 rows of 128 <= dpad <= 1024 (float32) or 256 <= dpad
+    // <= 1024 (bfloat16): each lane copies its own chunks (k_cand_knn_rows)
+    const int vpc = RK == 1 ? 8 : 4;
+    const int nchunk = idx->dpad / vpc;
+    if (RK != 2 && nchunk >= 32 && idx->dpad <= 1024) {
         const int U = (nchunk + 31) / 32;
-        auto kern = U == 1 ? k_cand_knn_bf16<KR, 1>
-                    : U == 2 ? k_cand_knn_bf16<KR, 2>
-                    : U == 3 ? k_cand_knn_bf16<KR, 3>
-                             : k_cand_knn_bf16<KR, 4>;
+        const void *kern = nullptr;
+        if (RK == 1 && rerank) {
+            kern = U == 1   ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 1, true>)
+                   : U == 2 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 1, true>)
+                   : U == 3 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 1, true>)
+                            : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 1, true>);
+        } else if (RK == 1) {
+            kern = U == 1   ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 1, false>)
+                   : U == 2 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 1, false>)
+                   : U == 3 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 1, false>)
+                            : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 1, false>);
+        } else {
+            const void *by_u[8] = {
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 5, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 6, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 7, 0, false>),
+                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 8, 0, false>)};
+            kern = by_u[U - 1];
+        }
         const size_t smem = size_t(CB_WARPS) * CB_SLOTS * 2 * size_t(nchunk) * 16;
-        e = launch_shape(reinterpret_cast<const void *>(kern), CB_WARPS * 32, smem, idx->device, &per_sm, &sms);
+        e = launch_shape(kern, CB_WARPS * 32, smem, idx->device, &per_sm, &sms);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((ql.m * 4 + CB_WARPS - 1) / CB_WARPS, int64_t(sms) * std::max(per_sm, 1)));
-        kern<<<unsigned(blocks), CB_WARPS * 32, smem, s>>>(a);
-        return cudaGetLastError();
+        void *args[] = {&a};
+        return cudaLaunchKernel(kern, dim3(unsigned(blocks)), dim3(CB_WARPS * 32), args, smem, s);
     }
     if (BF16 || CR_WARPS * per_warp <= 200 * 1024) {
         const size_t smem = CR_WARPS * per_warp;
