@@ -170,6 +170,16 @@ def kernel_source_sha(kernel: str, path: str) -> str:
     return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:16]
 
 
+def search_kernel_name(prec: int, d: int) -> str:
+    """The candidate-search kernel the library launches for rows of `d`
+    values in precision `prec` (0 float32, 1 bfloat16, 2 e4m3): per-lane
+    cp.async rows (k_cand_knn_rows) for float32 and bfloat16 rows of 32 or
+    64 to 1,024 padded values, whole-row bulk copies (k_cand_knn) otherwise."""
+    dpad = (d + 7) & ~7
+    nchunk = dpad // (8 if prec == 1 else 4)
+    return "k_cand_knn_rows" if prec != 2 and nchunk >= 8 and dpad <= 1024 else "k_cand_knn"
+
+
 def load_traffic(kernel: str, src: str, key: str = "dram_bytes_per_launch"):
     """A figure (DRAM bytes per launch by default) from the committed ncu
     summary of `kernel`, if it was taken on the kernel's current source
@@ -369,7 +379,7 @@ def run_gpu(args):
     r_vote = roof(vote_kernel, vote_bytes, vote_avg)
     rooflines = [r_vote]
     if args.path == 0:
-        r_search = roof("k_cand_knn", search_bytes, search_avg)
+        r_search = roof(search_kernel_name(prec, d), search_bytes, search_avg)
         # each candidate row once per step (rows reused across queries)
         uniq = min(n, mean_S * m) * d * 4
         r_search["frac_rows_once"] = round(

@@ -374,7 +374,12 @@ int mrpt_debug_fail_alloc_after(int32_t after);
 
 /* Fault injection for tests: each wait for a staged candidate row in the
  * candidate search's distance loop (path 0) gives up after `tries` tries
- * instead of about two million (negative restores the full bound).  A warp
+ * instead of about two million (negative restores the full bound).  Such
+ * waits (an mbarrier phase completed by a bulk copy of a whole row) exist
+ * only where the search copies whole rows: e4m3 rows, rows longer than
+ * 1,024 values, and rows shorter than 32 float32 or 64 bfloat16 values; the
+ * other rows are copied per lane with cp.async, whose per-thread waits
+ * always complete, and this setting does not affect them.  A warp
  * whose wait gives up stops, sets the index's status to MRPT_ERR_TIMEOUT
  * (reported by mrpt_sync, or by a call given host buffers) and first waits,
  * with the full bound, for its row copies still in flight; the rows of the

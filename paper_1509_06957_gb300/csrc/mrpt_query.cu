@@ -2252,8 +2252,27 @@ __device__ __forceinline__ float2 chunk_sq_acc(uint4 x, const float (&q)[4], flo
     return f32x4_sq_acc(x, q, acc);
 }
 
-// k_cand_knn for float32 rows (RT = 0) or bfloat16 rows (RT = 1) whose
-// 16-byte chunks (4 or 8 values) number between 32 (U - 1) + 1 and 32 U:
+// acc + (q - s x)^2 for the 16 e4m3 values of one 16-byte chunk x of a row
+// with scale s (ns = (-s, -s)) against 16 float32 query values: the values
+// are widened exactly, then t = q - s x is one fma (the product of a 4-bit
+// and a 24-bit significand needs no rounding), then acc += t t.
+__device__ __forceinline__ float2 e4m3x16_sq_acc(uint4 x, float2 ns, const float (&q)[16], float2 acc) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 v = e4m3x4_to_float4(w[j]);
+        float2 t = __ffma2_rn(ns, make_float2(v.x, v.y), make_float2(q[4 * j], q[4 * j + 1]));
+        acc = __ffma2_rn(t, t, acc);
+        t = __ffma2_rn(ns, make_float2(v.z, v.w), make_float2(q[4 * j + 2], q[4 * j + 3]));
+        acc = __ffma2_rn(t, t, acc);
+    }
+    return acc;
+}
+
+// k_cand_knn for float32 rows (RT = 0), bfloat16 rows (RT = 1) or e4m3 rows
+// with a per-row scale (RT = 2) whose
+// 16-byte chunks of values (4, 8 or 16 values) number between 32 (U - 1) + 1
+// and 32 U (or fewer than 32 with U = 1: lanes past the row idle):
 // one warp per (query, chunk of the list) work item, as in k_cand_knn, with
 // the rows in a per-warp ring of CB_SLOTS row pairs in shared memory.
 // - Lane l owns chunks l, l + 32, ... of every row. It copies its own chunks
@@ -2263,17 +2282,29 @@ __device__ __forceinline__ float2 chunk_sq_acc(uint4 x, const float (&q)[4], flo
 // - The query's chunks stay in registers for the whole item.
 // - Pairs are copied CB_SLOTS - 1 ahead. Each pair's two sums are reduced
 //   together and go into the warp's sorted top-k.
-// - With a lossy bfloat16 copy the item that completes a query re-ranks the
-//   k + margin survivors with float32 rows. Each survivor's row goes through
-//   the same ring, one row per slot. Lane l copies the two float32 chunks that
-//   cover its bfloat16 chunk's 8 values, so the query registers serve as they
-//   are.
+// - An e4m3 row's scale (the float32 after its values) is read by every lane
+//   with one broadcast load when the row's pair is copied, so it has arrived
+//   when the pair is summed.
+// - With a lossy copy (bfloat16 that does not hold X exactly, or e4m3) the
+//   item that completes a query re-ranks the k + margin survivors with
+//   float32 rows. Each survivor's row goes through the same ring, two rows in
+//   flight. Lane l copies the F = 2 or 4 float32 chunks that cover its
+//   chunk's 8 or 16 values, so the query registers serve as they are.
 constexpr int CB_WARPS = 4;
 constexpr int CB_SLOTS = 2;
 
+// 16-byte ring chunks per warp of k_cand_knn_rows for rows of `nchunk` value
+// chunks of `vpc` values: CB_SLOTS row pairs, and with a re-rank room for two
+// float32 rows (vpc / 4 float32 chunks per value chunk).
+__host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool rerank) {
+    return (rerank && 2 * (vpc / 4) > CB_SLOTS * 2 ? 2 * (vpc / 4) : CB_SLOTS * 2) * nchunk;
+}
+
 template <int KR, int U, int RT, bool RR>
 __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnArgs a0) {
-    constexpr int VPC = RT == 1 ? 8 : 4;  // values per 16-byte chunk
+    constexpr int VPC = RT == 2 ? 16 : RT == 1 ? 8 : 4;  // values per 16-byte chunk
+    constexpr int F = VPC / 4;  // float32 chunks per chunk (re-rank)
+    static_assert(!RR || RT != 0, "float32 rows need no re-rank");
     CandKnnArgs a = a0;
     if (a.rec != nullptr) {
         a.Q = a.rec->Q;
@@ -2284,9 +2315,11 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
     extern __shared__ __align__(16) unsigned char cbsm[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int nchunk = a.dpad / VPC;  // 16-byte chunks per row
+    // 16-byte chunks of values per row; an e4m3 row stores one more (its scale)
+    const int nchunk = RT == 2 ? int(a.row_bytes / 16u) - 1 : a.dpad / VPC;
+    const int rstride = RT == 2 ? nchunk + 1 : nchunk;
     const uint4 *Xb = reinterpret_cast<const uint4 *>(a.rows);
-    uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * (CB_SLOTS * 2) * nchunk;
+    uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * cb_ring_chunks(nchunk, VPC, RR);
     const uint32_t wring_s = smem_u32(wring);
     const int k = a.k;  // survivors kept (k + margin when re-ranking)
     const uint32_t n_items = *a.n_items;
@@ -2349,14 +2382,19 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
         };
         // copy pair p (rows 2p and 2p + 1; an odd item's last row twice) into
         // slot p % CB_SLOTS, one commit group per pair (empty past the item's
-        // last pair).  Rounds u < U - 1 are always inside the row
-        // (32 (U - 1) < dpad / 8), only the last one needs a bound.
-        auto issue_pair = [&](int p, int slot) {
+        // last pair), and load an e4m3 pair's scales into sc.  Rounds
+        // u < U - 1 are always inside the row (32 (U - 1) < nchunk), only the
+        // last one needs a bound.
+        auto issue_pair = [&](int p, int slot, float2 &sc) {
             if (2 * p < c) {
                 const int32_t id0 = id_of(2 * p);
                 const int32_t id1 = 2 * p + 1 < c ? id_of(2 * p + 1) : id0;
-                const uint4 *s0 = Xb + int64_t(id0) * nchunk + lane;
-                const uint4 *s1 = Xb + int64_t(id1) * nchunk + lane;
+                const uint4 *s0 = Xb + int64_t(id0) * rstride + lane;
+                const uint4 *s1 = Xb + int64_t(id1) * rstride + lane;
+                if (RT == 2) {
+                    sc.x = __ldg(reinterpret_cast<const float *>(Xb + int64_t(id0) * rstride + nchunk));
+                    sc.y = __ldg(reinterpret_cast<const float *>(Xb + int64_t(id1) * rstride + nchunk));
+                }
                 const uint32_t d0 = wring_s + uint32_t(slot * 2 * nchunk + lane) * 16u;
                 const uint32_t d1 = d0 + uint32_t(nchunk) * 16u;
 #pragma unroll
@@ -2373,13 +2411,17 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
         top.init();
         const int npairs = (c + 1) >> 1;
         int s_issue = 0, s_use = 0;  // slots of the next pair to copy and to use
+        // scales of the pairs in flight (e4m3): scs[j] for pair p + j
+        float2 scs[CB_SLOTS];
+#pragma unroll
+        for (int j = 0; j < CB_SLOTS; ++j) scs[j] = make_float2(1.f, 1.f);
 #pragma unroll
         for (int p = 0; p < CB_SLOTS - 1; ++p) {
-            issue_pair(p, s_issue);
+            issue_pair(p, s_issue, scs[p]);
             s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
         }
         for (int p = 0; p < npairs; ++p) {
-            issue_pair(p + CB_SLOTS - 1, s_issue);
+            issue_pair(p + CB_SLOTS - 1, s_issue, scs[CB_SLOTS - 1]);
             s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
             // this thread's copies of pair p are in (groups of later pairs may not be)
             asm volatile("cp.async.wait_group %0;" ::"n"(CB_SLOTS - 1) : "memory");
@@ -2387,14 +2429,22 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
             const uint4 *r1 = r0 + nchunk;
             s_use = s_use + 1 == CB_SLOTS ? 0 : s_use + 1;
             float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            const float2 ns0 = make_float2(-scs[0].x, -scs[0].x), ns1 = make_float2(-scs[0].y, -scs[0].y);
+#pragma unroll
+            for (int j = 0; j + 1 < CB_SLOTS; ++j) scs[j] = scs[j + 1];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool in = u < U - 1 || lane + 32 * u < nchunk;
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 const uint4 x0 = in ? r0[32 * u] : z;
                 const uint4 x1 = in ? r1[32 * u] : z;
-                a0 = chunk_sq_acc(x0, qv[u], a0);
-                a1 = chunk_sq_acc(x1, qv[u], a1);
+                if constexpr (RT == 2) {
+                    a0 = e4m3x16_sq_acc(x0, ns0, qv[u], a0);
+                    a1 = e4m3x16_sq_acc(x1, ns1, qv[u], a1);
+                } else {
+                    a0 = chunk_sq_acc(x0, qv[u], a0);
+                    a1 = chunk_sq_acc(x1, qv[u], a1);
+                }
             }
             float d0, d1;
             warp_sum2(a0.x + a0.y, a1.x + a1.y, lane, d0, d1);
@@ -2443,11 +2493,13 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
                 }
             }
         }
-        if (RT == 1 && RR && finish) {
+        if (RR && finish) {
             // re-rank: exact float32 distances of the k + margin survivors,
-            // one float32 row per ring slot, the next row copied while this
+            // two float32 rows in the ring, the next row copied while this
             // one is summed; keep the kfinal smallest
-            const uint4 *Xf = reinterpret_cast<const uint4 *>(a.X);  // 2 nchunk chunks per row
+            const uint4 *Xf = reinterpret_cast<const uint4 *>(a.X);
+            const int fstride = a.dpad / 4;  // float32 chunks per row of X
+            const int fslot = F * nchunk;    // ring chunks per float32 row
             auto sid = [&](int f) -> int32_t {
                 int32_t v = SENTINEL_ID;
 #pragma unroll
@@ -2461,15 +2513,22 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
 #pragma unroll
             for (int rr = 0; rr < KR; ++rr)
                 nsurv += __popc(__ballot_sync(0xffffffffu, rr * 32 + lane < k && top.i[rr] != SENTINEL_ID));
+            // lane l's float32 chunks F (l + 32 u) + h; those past the row of
+            // X (an e4m3 row's last chunk can reach beyond dpad) read as zero
             auto issue_row = [&](int f) {
                 if (f < nsurv) {
-                    const uint4 *src = Xf + int64_t(sid(f)) * (2 * nchunk) + 2 * lane;
-                    const uint32_t dst = wring_s + uint32_t((f & 1) * 2 * nchunk + 2 * lane) * 16u;
+                    const uint4 *src = Xf + int64_t(sid(f)) * fstride;
+                    const uint32_t dst = wring_s + uint32_t((f & 1) * fslot + F * lane) * 16u;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         if (u < U - 1 || lane + 32 * u < nchunk) {
-                            cp_async16_zfill(dst + uint32_t(64 * u) * 16u, src + 64 * u, 16u);
-                            cp_async16_zfill(dst + uint32_t(64 * u + 1) * 16u, src + 64 * u + 1, 16u);
+#pragma unroll
+                            for (int h = 0; h < F; ++h) {
+                                const int fc = F * (lane + 32 * u) + h;
+                                const bool inrow = RT != 2 || fc < fstride;
+                                cp_async16_zfill(dst + uint32_t(32 * F * u + h) * 16u, inrow ? src + fc : src,
+                                                 inrow ? 16u : 0u);
+                            }
                         }
                     }
                 }
@@ -2481,13 +2540,13 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
             for (int f = 0; f < nsurv; ++f) {
                 issue_row(f + 1);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
-                const uint4 *row = wring + (f & 1) * 2 * nchunk + 2 * lane;
+                const uint4 *row = wring + (f & 1) * fslot + F * lane;
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (u < U - 1 || lane + 32 * u < nchunk) {
-                        acc = f32x4_sq_acc(row[64 * u], qv[u], acc);
-                        acc = f32x4_sq_acc(row[64 * u + 1], qv[u] + 4, acc);
+#pragma unroll
+                        for (int h = 0; h < F; ++h) acc = f32x4_sq_acc(row[32 * F * u + h], qv[u] + 4 * h, acc);
                     }
                 }
                 float e0, e1;
@@ -2802,14 +2861,19 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     a.cand_off = ql.cand_off;
     int sms = 0, per_sm = 0;
     cudaError_t e;
-    // float32 or bfloat16 rows of 128 <= dpad <= 1024 (float32) or 256 <= dpad
-    // <= 1024 (bfloat16): each lane copies its own chunks (k_cand_knn_rows)
-    const int vpc = RK == 1 ? 8 : 4;
-    const int nchunk = idx->dpad / vpc;
-    if (RK != 2 && nchunk >= 32 && idx->dpad <= 1024) {
+    // rows of at least 8 16-byte chunks of values (float32 dpad >= 32,
+    // bfloat16 dpad >= 64, e4m3 dpad > 112) and dpad <= 1024: each lane
+    // copies its own chunks (k_cand_knn_rows; with fewer than 32 chunks per
+    // row the lanes past them idle)
+    const int vpc = RK == 2 ? 16 : RK == 1 ? 8 : 4;
+    const int nchunk = RK == 2 ? int(row_bytes / 16) - 1 : idx->dpad / vpc;
+    if (nchunk >= 8 && idx->dpad <= 1024) {
         const int U = (nchunk + 31) / 32;
         const void *kern = nullptr;
-        if (RK == 1 && rerank) {
+        if (RK == 2) {
+            kern = U == 1 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 2, true>)
+                          : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 2, true>);
+        } else if (RK == 1 && rerank) {
             kern = U == 1   ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 1, true>)
                    : U == 2 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 1, true>)
                    : U == 3 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 1, true>)
@@ -2831,7 +2895,7 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
                 reinterpret_cast<const void *>(k_cand_knn_rows<KR, 8, 0, false>)};
             kern = by_u[U - 1];
         }
-        const size_t smem = size_t(CB_WARPS) * CB_SLOTS * 2 * size_t(nchunk) * 16;
+        const size_t smem = size_t(CB_WARPS) * size_t(cb_ring_chunks(nchunk, vpc, rerank)) * 16;
         e = launch_shape(kern, CB_WARPS * 32, smem, idx->device, &per_sm, &sms);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(

@@ -113,3 +113,18 @@ def test_reduced_copy_emulation_and_distance_error():
             dl = ((X8[j] - Q[i].double()) ** 2).sum()
             want.append(float(abs(dl - d64) / d64))
     assert abs(emax - max(want)) < 1e-12 and abs(emean - sum(want) / len(want)) < 1e-12
+
+
+def test_search_kernel_name_follows_the_dispatch_rule():
+    """bench.py names the search kernel of its roofline by the library's
+    dispatch rule; the rule's condition must still read as bench.py assumes."""
+    src = open(SRC).read()
+    assert "if (RK != 2 && nchunk >= 8 && idx->dpad <= 1024) {" in src
+    assert "const int vpc = RK == 1 ? 8 : 4;" in src
+    cases = {(0, 784): "k_cand_knn_rows", (1, 784): "k_cand_knn_rows", (2, 784): "k_cand_knn",
+             (0, 1024): "k_cand_knn_rows", (0, 1025): "k_cand_knn", (1, 1100): "k_cand_knn",
+             (0, 25): "k_cand_knn_rows", (0, 24): "k_cand_knn", (1, 64): "k_cand_knn_rows",
+             (1, 56): "k_cand_knn"}
+    for (prec, d), name in cases.items():
+        assert bench.search_kernel_name(prec, d) == name, (prec, d)
+        assert bench.kernel_source_sha(name, SRC)

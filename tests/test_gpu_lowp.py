@@ -159,3 +159,57 @@ def test_large_candidate_sets_float32_match_oracle(mr):
     oi, od, _, oleaf, _ = oracle.query(ref, Q, k, v, want_internals=True)
     check_results(X, Q, ids, d, oi, od, oracle_sets(ref, oleaf, v))
     idx.close()
+
+
+def _emulated_recall(X, Q, sets, oi, od, k, margin):
+    """Tie-aware recall of a float64 emulation of the e4m3 screen: the
+    k + margin members of S nearest by the e4m3 copy's distances, re-ranked
+    exactly, the k nearest kept."""
+    import bench
+    Xl = bench.lowp_copy(torch.from_numpy(X), 2, torch).numpy()
+    hit = total = 0
+    for i, s in enumerate(sets):
+        ids = np.array(sorted(s), dtype=np.int64)
+        q = Q[i].astype(np.float64)
+        screen = ((Xl[ids] - q) ** 2).sum(1)
+        keep = ids[np.lexsort((ids, screen))[:k + margin]]
+        exact = ((X[keep].astype(np.float64) - q) ** 2).sum(1)
+        best = keep[np.lexsort((keep, exact))[:k]]
+        fin = np.isfinite(od[i])
+        if not fin.any():
+            continue
+        kth = od[i][fin][-1]
+        dist = np.sqrt(((X[best].astype(np.float64) - q) ** 2).sum(1))
+        hit += min(int((dist <= kth * (1 + 1e-6)).sum()), int(fin.sum()))
+        total += int(fin.sum())
+    return hit / total
+
+
+@pytest.mark.parametrize("d,k,margin", [(200, 10, 16), (520, 40, 24), (1000, 100, 32)],
+                         ids=["d200-k10", "d520-k40", "d1000-k100"])
+def test_fp8_rows_of_one_and_two_rounds(mr, d, k, margin):
+    """e4m3 rows in the per-lane copy kernel: 13, 33 and 63 chunks of 16
+    values per row (one round of the lanes, two rounds, two rounds nearly
+    full), rows whose last chunk reaches past the float32 row (d = 200 and
+    520 are not multiples of 16, so the re-rank reads zeros there), k above
+    32, and lists of thousands of candidates split into several work items.
+    Checked against the oracle: ids in S, exact float32 distances, ascending
+    rows, |S| equal, and recall no more than 0.02 below a float64 emulation
+    of the same e4m3 screen."""
+    from _parity import check_lowp_results
+    X, Q = workloads.latent_factor(6000, d, 60, seed=11)
+    T, l, v = 24, 4, 2
+    dens = float(np.float32(d ** -0.5))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, dens, 9)
+    mr.mrpt_add_lowp(idx, mr.MRPT_PREC_FP8)
+    ids, dd, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, precision=mr.MRPT_PREC_FP8,
+                                    margin=margin, debug=True)
+    torch.cuda.synchronize()
+    ref = oracle.grow_trees(X, T, l, dens, 9)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, k, v, want_internals=True)
+    assert np.array_equal(dbg["n_cand"].cpu().numpy(), oncand)
+    assert oncand.min() > 600
+    sets = oracle_sets(ref, oleaf, v)
+    floor = _emulated_recall(X, Q, sets, oi, od, k, margin) - 0.02
+    check_lowp_results(X, Q, ids.cpu().numpy(), dd.cpu().numpy(), oi, od, sets, floor)
+    idx.close()
