@@ -173,11 +173,12 @@ def kernel_source_sha(kernel: str, path: str) -> str:
 def search_kernel_name(prec: int, d: int) -> str:
     """The candidate-search kernel the library launches for rows of `d`
     values in precision `prec` (0 float32, 1 bfloat16, 2 e4m3): per-lane
-    cp.async rows (k_cand_knn_rows) for float32 and bfloat16 rows of 32 or
-    64 to 1,024 padded values, whole-row bulk copies (k_cand_knn) otherwise."""
+    cp.async rows (k_cand_knn_rows) for rows of at least 8 16-byte chunks
+    of values and at most 1,024 padded values, whole-row bulk copies
+    (k_cand_knn) otherwise."""
     dpad = (d + 7) & ~7
-    nchunk = dpad // (8 if prec == 1 else 4)
-    return "k_cand_knn_rows" if prec != 2 and nchunk >= 8 and dpad <= 1024 else "k_cand_knn"
+    nchunk = (dpad + 15) // 16 if prec == 2 else dpad // (8 if prec == 1 else 4)
+    return "k_cand_knn_rows" if nchunk >= 8 and dpad <= 1024 else "k_cand_knn"
 
 
 def load_traffic(kernel: str, src: str, key: str = "dram_bytes_per_launch"):

@@ -376,8 +376,8 @@ int mrpt_debug_fail_alloc_after(int32_t after);
  * candidate search's distance loop (path 0) gives up after `tries` tries
  * instead of about two million (negative restores the full bound).  Such
  * waits (an mbarrier phase completed by a bulk copy of a whole row) exist
- * only where the search copies whole rows: e4m3 rows, rows longer than
- * 1,024 values, and rows shorter than 32 float32 or 64 bfloat16 values; the
+ * only where the search copies whole rows: rows longer than 1,024 values,
+ * and rows shorter than 32 float32, 64 bfloat16 or 113 e4m3 values; the
  * other rows are copied per lane with cp.async, whose per-thread waits
  * always complete, and this setting does not affect them.  A warp
  * whose wait gives up stops, sets the index's status to MRPT_ERR_TIMEOUT

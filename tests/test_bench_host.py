@@ -119,9 +119,12 @@ def test_search_kernel_name_follows_the_dispatch_rule():
     """bench.py names the search kernel of its roofline by the library's
     dispatch rule; the rule's condition must still read as bench.py assumes."""
     src = open(SRC).read()
-    assert "if (RK != 2 && nchunk >= 8 && idx->dpad <= 1024) {" in src
-    assert "const int vpc = RK == 1 ? 8 : 4;" in src
-    cases = {(0, 784): "k_cand_knn_rows", (1, 784): "k_cand_knn_rows", (2, 784): "k_cand_knn",
+    assert "if (nchunk >= 8 && idx->dpad <= 1024) {" in src
+    assert "const int nchunk = RK == 2 ? int(row_bytes / 16) - 1 : idx->dpad / vpc;" in src
+    assert "idx->row8_bytes = ((idx->dpad + 15) & ~15) + 16;" in src
+    cases = {(0, 784): "k_cand_knn_rows", (1, 784): "k_cand_knn_rows", (2, 784): "k_cand_knn_rows",
+             (2, 113): "k_cand_knn_rows", (2, 112): "k_cand_knn", (2, 64): "k_cand_knn",
+             (2, 1100): "k_cand_knn",
              (0, 1024): "k_cand_knn_rows", (0, 1025): "k_cand_knn", (1, 1100): "k_cand_knn",
              (0, 25): "k_cand_knn_rows", (0, 24): "k_cand_knn", (1, 64): "k_cand_knn_rows",
              (1, 56): "k_cand_knn"}
