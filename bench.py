@@ -617,8 +617,11 @@ def run_large(args):
     of the k + 32 nearest (skipped for a lossless bfloat16 copy).  Each point
     reports tie-aware recall@k against a float64 brute force, the recall loss
     against float32 at the same v, the relative error of the reduced copy's
-    squared distances against float64 at the returned neighbours (max, mean)
-    and queries/s of device time (L2 flushed before the timed pass)."""
+    squared distances against float64 at the returned neighbours (max, mean),
+    queries/s of device time (L2 flushed before the timed pass), the
+    candidate search's time, the mean |S| and the search's algorithmic bytes
+    per second (rows in the precision used, lists, queries, outputs and
+    re-rank rows)."""
     import torch
     import paper_1509_06957_gb300 as mr
     dev = torch.device("cuda", 0)
@@ -646,14 +649,24 @@ def run_large(args):
         rows = []
         for v in range(1, 11):
             rec32 = None
+            ncand = torch.empty(m, dtype=torch.int64, device=dev)
+            mr.mrpt_query_ex(index, Q, k, v, n_cand_out=ncand)
+            mean_S = float(ncand.double().mean())
             for prec, margin in precs:
                 mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin)  # warm
                 flush.zero_()
                 ids, dists = mr.mrpt_query_ex(index, Q, k, v, precision=prec, margin=margin, stage_ms=stage)
                 rec = float(((dists <= kth * (1 + 1e-5)) & torch.isfinite(dists)).sum()) / (m * k)
+                # the search's algorithmic bytes per query: candidate rows
+                # (+ e4m3 scale chunk), list, query, output, re-rank rows
+                reranked = prec == 2 or (prec == 1 and not bf16_exact)
+                sbytes = (mean_S * (d * (4, 2, 1)[prec] + (16 if prec == 2 else 0) + 4) + d * 4 + k * 8
+                          + (min(k + margin, mean_S) * d * 4 if reranked else 0))
                 row = dict(v=v, precision=("fp32", "bf16", "fp8")[prec], margin=margin,
                            recall=round(rec, 4), qps=round(m / (float(stage[3]) / 1e3), 1),
-                           ms=round(float(stage[3]), 3))
+                           ms=round(float(stage[3]), 3), search_ms=round(float(stage[2]), 3),
+                           mean_S=round(mean_S, 1),
+                           search_gbs=round(sbytes * m / (float(stage[2]) / 1e3) / 1e9, 1))
                 if prec == 0:
                     rec32 = rec
                 else:

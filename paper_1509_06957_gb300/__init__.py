@@ -229,6 +229,24 @@ def _check_matrix(name: str, x, rows: int, cols: int, dtype) -> None:
         raise ValueError(f"{name} must be contiguous (row-major, tightly packed)")
 
 
+def _check_vector(name: str, x, size: int, dtype) -> None:
+    """x must be a contiguous vector of `size` elements of `dtype` (the C ABI
+    writes that many)."""
+    if _is_torch(x):
+        import torch
+        ok_type = x.dtype == {np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        contiguous = x.is_contiguous()
+    else:
+        ok_type = np.dtype(x.dtype) == np.dtype(dtype)
+        contiguous = bool(x.flags["C_CONTIGUOUS"])
+    if tuple(x.shape) != (size,):
+        raise ValueError(f"{name} must have shape ({size},), got {tuple(x.shape)}")
+    if not ok_type:
+        raise ValueError(f"{name} must be {np.dtype(dtype).name}, got {x.dtype}")
+    if not contiguous:
+        raise ValueError(f"{name} must be contiguous")
+
+
 def _check_queries(Q, index) -> int:
     """Q must be an m x d matrix for an index of dimension d; returns m."""
     if len(Q.shape) != 2:
@@ -371,11 +389,13 @@ def mrpt_info(index: Index) -> IndexInfo:
 def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
                   out_dists=None, debug: bool = False, cand_cap: int | None = None,
                   stage_ms=None, path: int = 0, precision: int = 0, margin: int = 0,
-                  chunk: int = 0, ring: int = 0):
+                  chunk: int = 0, ring: int = 0, n_cand_out=None):
     """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
     tensors for a CUDA tensor, numpy arrays for host input) unless given.
     With ``debug`` also returns a dict of the internals: proj, leaf, votes,
-    n_cand and cand (members of S, row padded).  ``stage_ms`` (a float32
+    n_cand and cand (members of S, row padded).  ``n_cand_out`` (m int64,
+    device or host) receives |S| of every query on its own, without the
+    m x n debug buffers.  ``stage_ms`` (a float32
     numpy array of 4) receives the routing, voting, candidate-search and
     total device times of this call in ms.  ``path`` 0 runs the vote/emit
     and candidate-search kernels, 1 the fused kernel.  ``precision``
@@ -403,6 +423,10 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
     if stage_ms is not None:
         assert stage_ms.dtype == np.float32 and stage_ms.size >= 4
         opts.stage_ms = stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    if n_cand_out is not None:
+        assert not debug, "n_cand_out: debug already returns n_cand"
+        _check_vector("n_cand_out", n_cand_out, m, np.int64)
+        opts.n_cand = _ptr(n_cand_out).value
     dbg = None
     if debug:
         T_use = n_trees if n_trees > 0 else index.T

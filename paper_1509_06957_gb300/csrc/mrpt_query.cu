@@ -1689,6 +1689,53 @@ __device__ __forceinline__ uint32_t vote4h(uint32_t cnt_s, int4 e, uint32_t ok, 
     return hit;
 }
 
+// vote4h for a lane whose four entries all lie in the leaf (no spare-word
+// select): the same increments, old counts and test.
+__device__ __forceinline__ uint32_t vote4f(uint32_t cnt_s, int4 e, uint32_t vm1x4, uint32_t &x) {
+    uint32_t hit;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred h;\n\t"
+        ".reg .b32 t<4>, n<4>, r<4>, z, one;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "mov.b32 one, 1;\n\t"
+        "prmt.b32.b4e n0, one, z, %2;\n\t"
+        "prmt.b32.b4e n1, one, z, %3;\n\t"
+        "prmt.b32.b4e n2, one, z, %4;\n\t"
+        "prmt.b32.b4e n3, one, z, %5;\n\t"
+        "and.b32 t0, %2, 0xfffffffc;\n\t"
+        "and.b32 t1, %3, 0xfffffffc;\n\t"
+        "and.b32 t2, %4, 0xfffffffc;\n\t"
+        "and.b32 t3, %5, 0xfffffffc;\n\t"
+        "add.u32 t0, t0, %6;\n\t"
+        "add.u32 t1, t1, %6;\n\t"
+        "add.u32 t2, t2, %6;\n\t"
+        "add.u32 t3, t3, %6;\n\t"
+        "atom.shared.add.u32 r0, [t0], n0;\n\t"
+        "atom.shared.add.u32 r1, [t1], n1;\n\t"
+        "atom.shared.add.u32 r2, [t2], n2;\n\t"
+        "atom.shared.add.u32 r3, [t3], n3;\n\t"
+        "prmt.b32.f4e r0, r0, z, %2;\n\t"
+        "prmt.b32.f4e r1, r1, z, %3;\n\t"
+        "prmt.b32.f4e r2, r2, z, %4;\n\t"
+        "prmt.b32.f4e r3, r3, z, %5;\n\t"
+        "prmt.b32 r0, r0, r1, 0x0040;\n\t"
+        "prmt.b32 r2, r2, r3, 0x0040;\n\t"
+        "prmt.b32 r0, r0, r2, 0x5410;\n\t"
+        "xor.b32 %1, r0, %7;\n\t"
+        "sub.u32 r1, %1, 0x01010101;\n\t"
+        "not.b32 r2, %1;\n\t"
+        "and.b32 r1, r1, r2;\n\t"
+        "and.b32 r1, r1, 0x80808080;\n\t"
+        "setp.ne.u32 h, r1, 0;\n\t"
+        "selp.u32 %0, 1, 0, h;\n\t"
+        "}"
+        : "=r"(hit), "=r"(x)
+        : "r"(e.x), "r"(e.y), "r"(e.z), "r"(e.w), "r"(cnt_s), "r"(vm1x4)
+        : "memory");
+    return hit;
+}
+
 // k_vote_emit for an index whose ids fit one counter array (n <= 65,536),
 // over the vote layout: every leaf starts on a 16-byte boundary and is padded
 // with the sentinel to a multiple of 4 ids, so a lane's 16-byte load is four
@@ -1697,6 +1744,10 @@ __device__ __forceinline__ uint32_t vote4h(uint32_t cnt_s, int4 e, uint32_t ok, 
 // units); every leaf spans the same number a.win of windows, and window i of
 // the query is window i % win of tree i / win.  Warp w takes windows w,
 // w + 16, w + 32, ... two at a time (four loads in flight before any vote).
+// ONE: every leaf is one window (win = 1: window i is tree i's leaf) of at
+// least 32 16-byte units, so the first 32 units of every window lie in the
+// leaf and vote with no range select.
+template <bool ONE>
 __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs a0) {
     VoteEmitArgs a = a0;
     if (a.rec != nullptr) a.m = a.rec->m;
@@ -1768,19 +1819,34 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_flat(const VoteEmitArgs 
             }
         };
         for (int i = warp; i < W; i += VE_WARPS) {
-            const int t0 = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32);
-            const int j0 = (i - t0 * K) * 64 + lane;
-            const int2 s0 = seg[t0];
-            const uint32_t ok00 = j0 < s0.y, ok01 = j0 + 32 < s0.y;
-            const int4 *p0 = a.leaf4 + (s0.x + j0);
-            const int4 q00 = ldg4_if(p0, ok00);
-            const int4 q01 = ldg4_if(p0 + 32, ok01);
-            uint32_t o00, o01;
-            const uint32_t h0 = vote4h(cnt_s, q00, ok00, vm1x4, spare, o00);
-            const uint32_t h1 = vote4h(cnt_s, q01, ok01, vm1x4, spare, o01);
-            if (__any_sync(0xffffffffu, (h0 | h1) != 0u)) {
-                if (h0) emit(q00, o00);
-                if (h1) emit(q01, o01);
+            if constexpr (ONE) {
+                const int2 s0 = seg[i];
+                const uint32_t ok01 = lane + 32 < s0.y;
+                const int4 *p0 = a.leaf4 + (s0.x + lane);
+                const int4 q00 = __ldg(p0);
+                const int4 q01 = ldg4_if(p0 + 32, ok01);
+                uint32_t o00, o01;
+                const uint32_t h0 = vote4f(cnt_s, q00, vm1x4, o00);
+                const uint32_t h1 = vote4h(cnt_s, q01, ok01, vm1x4, spare, o01);
+                if (__any_sync(0xffffffffu, (h0 | h1) != 0u)) {
+                    if (h0) emit(q00, o00);
+                    if (h1) emit(q01, o01);
+                }
+            } else {
+                const int t0 = int((uint64_t(uint32_t(i)) * a.win_magic) >> 32);
+                const int j0 = (i - t0 * K) * 64 + lane;
+                const int2 s0 = seg[t0];
+                const uint32_t ok00 = j0 < s0.y, ok01 = j0 + 32 < s0.y;
+                const int4 *p0 = a.leaf4 + (s0.x + j0);
+                const int4 q00 = ldg4_if(p0, ok00);
+                const int4 q01 = ldg4_if(p0 + 32, ok01);
+                uint32_t o00, o01;
+                const uint32_t h0 = vote4h(cnt_s, q00, ok00, vm1x4, spare, o00);
+                const uint32_t h1 = vote4h(cnt_s, q01, ok01, vm1x4, spare, o01);
+                if (__any_sync(0xffffffffu, (h0 | h1) != 0u)) {
+                    if (h0) emit(q00, o00);
+                    if (h1) emit(q01, o01);
+                }
             }
         }
         if (qn >= 0 && tid < T) {
@@ -2300,8 +2366,13 @@ __host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool reran
     return (rerank && 2 * (vpc / 4) > CB_SLOTS * 2 ? 2 * (vpc / 4) : CB_SLOTS * 2) * nchunk;
 }
 
+// Blocks per SM that k_cand_knn_rows is compiled for (its register cap):
+// 6 for k <= 64, which keeps the loop's latency hidden by more resident warps
+// (measured against the compiler's default); larger k keeps the default.
+__host__ __device__ constexpr int cb_min_blocks(int kr) { return kr <= 2 ? 6 : 1; }
+
 template <int KR, int U, int RT, bool RR>
-__global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnArgs a0) {
+__global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_rows(const CandKnnArgs a0) {
     constexpr int VPC = RT == 2 ? 16 : RT == 1 ? 8 : 4;  // values per 16-byte chunk
     constexpr int F = VPC / 4;  // float32 chunks per chunk (re-rank)
     static_assert(!RR || RT != 0, "float32 rows need no re-rank");
@@ -2514,11 +2585,17 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
             for (int rr = 0; rr < KR; ++rr)
                 nsurv += __popc(__ballot_sync(0xffffffffu, rr * 32 + lane < k && top.i[rr] != SENTINEL_ID));
             // lane l's float32 chunks F (l + 32 u) + h; those past the row of
-            // X (an e4m3 row's last chunk can reach beyond dpad) read as zero
+            // X (an e4m3 row's last chunk can reach beyond dpad) read as zero.
+            // In the ring, chunk h of round u sits at 32 F u + h w_u + l, w_u
+            // the lanes of round u (32, or wl in the last): for each (u, h)
+            // the lanes touch consecutive 16-byte slots, so neither the
+            // copies nor the reads meet bank conflicts.
+            const int wl = nchunk - 32 * (U - 1);
+            auto slot_of = [&](int u, int h) -> int { return 32 * F * u + h * (u < U - 1 ? 32 : wl) + lane; };
             auto issue_row = [&](int f) {
                 if (f < nsurv) {
                     const uint4 *src = Xf + int64_t(sid(f)) * fstride;
-                    const uint32_t dst = wring_s + uint32_t((f & 1) * fslot + F * lane) * 16u;
+                    const uint32_t dst = wring_s + uint32_t((f & 1) * fslot) * 16u;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         if (u < U - 1 || lane + 32 * u < nchunk) {
@@ -2526,7 +2603,7 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
                             for (int h = 0; h < F; ++h) {
                                 const int fc = F * (lane + 32 * u) + h;
                                 const bool inrow = RT != 2 || fc < fstride;
-                                cp_async16_zfill(dst + uint32_t(32 * F * u + h) * 16u, inrow ? src + fc : src,
+                                cp_async16_zfill(dst + uint32_t(slot_of(u, h)) * 16u, inrow ? src + fc : src,
                                                  inrow ? 16u : 0u);
                             }
                         }
@@ -2540,13 +2617,13 @@ __global__ void __launch_bounds__(CB_WARPS * 32) k_cand_knn_rows(const CandKnnAr
             for (int f = 0; f < nsurv; ++f) {
                 issue_row(f + 1);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
-                const uint4 *row = wring + (f & 1) * fslot + F * lane;
+                const uint4 *row = wring + (f & 1) * fslot;
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (u < U - 1 || lane + 32 * u < nchunk) {
 #pragma unroll
-                        for (int h = 0; h < F; ++h) acc = f32x4_sq_acc(row[32 * F * u + h], qv[u] + 4 * h, acc);
+                        for (int h = 0; h < F; ++h) acc = f32x4_sq_acc(row[slot_of(u, h)], qv[u] + 4 * h, acc);
                     }
                 }
                 float e0, e1;
@@ -2765,7 +2842,12 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     const int64_t leaf_len = (idx->n + idx->L - 1) / idx->L;
     const int64_t chunks = (idx->n + CH_IDS - 1) / CH_IDS;
     const bool packed = !flat && leaf_len < 48 * chunks;
-    auto kern = flat ? k_vote_flat : packed ? k_vote_packed : k_vote_emit;
+    // one window per leaf and at least 32 16-byte units in every leaf: leaf
+    // sizes at depth l are floor(n / 2^l) or one more, and units are
+    // ceil(size / 4) (the vote layout pads with the sentinel)
+    const int64_t min_units = (idx->n / idx->L + 3) / 4;
+    const bool one = flat && (idx->vote_win + 1) / 2 <= 1 && min_units >= 32;
+    auto kern = flat ? (one ? k_vote_flat<true> : k_vote_flat<false>) : packed ? k_vote_packed : k_vote_emit;
     const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 8
                         : packed ? size_t(cnt_words + 32) * 4 + size_t(4 * ql.n_trees + 1) * 4
                                  : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +

@@ -53,6 +53,18 @@ def test_output_buffers_must_be_m_by_k(index, name, ids, dists):
         mr.mrpt_query_ex(index, Q, 3, 1, out_ids=ids, out_dists=dists)
 
 
+@pytest.mark.parametrize("ncand", [
+    np.zeros(4, np.int64),                    # too short
+    np.zeros(5, np.int32),                    # wrong type
+    np.zeros((5, 1), np.int64),               # not a vector
+    np.zeros(10, np.int64)[::2],              # not contiguous
+])
+def test_n_cand_out_must_be_m_int64(index, ncand):
+    Q = np.zeros((5, 8), np.float32)
+    with pytest.raises(ValueError, match="n_cand_out"):
+        mr.mrpt_query_ex(index, Q, 3, 1, n_cand_out=ncand)
+
+
 def test_noalloc_checks_its_buffers(index):
     Q = torch.zeros((5, 8))
     ok_i, ok_d = torch.zeros((5, 3), dtype=torch.int32), torch.zeros((5, 3))

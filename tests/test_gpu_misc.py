@@ -119,3 +119,27 @@ def test_host_buffers_large_batch_chunked_upload(mr):
     check_results(X, Q, b[0], b[1], oi, od, sets)
     check_results(X, Q, a[0].cpu().numpy(), a[1].cpu().numpy(), oi, od, sets)
     idx.close()
+
+
+@pytest.mark.parametrize("host", [False, True], ids=["device", "host"])
+def test_n_cand_out_alone_is_the_oracle_count(mr, host):
+    """|S| of every query through n_cand_out alone (no m x n debug buffers),
+    device and host buffers, equals the oracle's count, and the rows are the
+    oracle's."""
+    X, Q = workloads.gaussian_mixture(5000, 40, 300, n_centres=10, seed=21)
+    T, l, v, k = 12, 5, 3, 8
+    dens = float(np.float32(40 ** -0.5))
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T, l, dens, 4)
+    ref = oracle.grow_trees(X, T, l, dens, 4)
+    oi, od, _, oleaf, oncand = oracle.query(ref, Q, k, v, want_internals=True)
+    if host:
+        ncand = np.full(len(Q), -7, np.int64)
+        gi, gd = mr.mrpt_query_ex(idx, Q, k, v, n_cand_out=ncand)
+    else:
+        ncand_d = torch.full((len(Q),), -7, dtype=torch.int64, device="cuda")
+        gi, gd = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, n_cand_out=ncand_d)
+        torch.cuda.synchronize()
+        ncand, gi, gd = ncand_d.cpu().numpy(), gi.cpu().numpy(), gd.cpu().numpy()
+    assert np.array_equal(ncand, oncand)
+    check_results(X, Q, gi, gd, oi, od, oracle_sets(ref, oleaf, v))
+    idx.close()
