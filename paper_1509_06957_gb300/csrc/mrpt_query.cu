@@ -2367,9 +2367,9 @@ __host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool reran
 }
 
 // Blocks per SM that k_cand_knn_rows is compiled for (its register cap):
-// 6 for k <= 64, which keeps the loop's latency hidden by more resident warps
+// 7 for k <= 64, which keeps the loop's latency hidden by more resident warps
 // (measured against the compiler's default); larger k keeps the default.
-__host__ __device__ constexpr int cb_min_blocks(int kr) { return kr <= 2 ? 6 : 1; }
+__host__ __device__ constexpr int cb_min_blocks(int kr) { return kr <= 2 ? 7 : 1; }
 
 template <int KR, int U, int RT, bool RR>
 __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_rows(const CandKnnArgs a0) {
