@@ -2360,10 +2360,10 @@ constexpr int CB_WARPS = 4;
 constexpr int CB_SLOTS = 2;
 
 // 16-byte ring chunks per warp of k_cand_knn_rows for rows of `nchunk` value
-// chunks of `vpc` values: CB_SLOTS row pairs, and with a re-rank room for two
-// float32 rows (vpc / 4 float32 chunks per value chunk).
-__host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool rerank) {
-    return (rerank && 2 * (vpc / 4) > CB_SLOTS * 2 ? 2 * (vpc / 4) : CB_SLOTS * 2) * nchunk;
+// chunks of `vpc` values, `rows` rows per step: CB_SLOTS steps, and with a
+// re-rank room for two float32 rows (vpc / 4 float32 chunks per value chunk).
+__host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool rerank, int rows) {
+    return (rerank && 2 * (vpc / 4) > CB_SLOTS * rows ? 2 * (vpc / 4) : CB_SLOTS * rows) * nchunk;
 }
 
 // Blocks per SM that k_cand_knn_rows is compiled for (its register cap):
@@ -2371,11 +2371,14 @@ __host__ __device__ constexpr int cb_ring_chunks(int nchunk, int vpc, bool reran
 // (measured against the compiler's default); larger k keeps the default.
 __host__ __device__ constexpr int cb_min_blocks(int kr) { return kr <= 2 ? 7 : 1; }
 
-template <int KR, int U, int RT, bool RR>
+template <int KR, int U, int RT, bool RR, int G>
 __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_rows(const CandKnnArgs a0) {
     constexpr int VPC = RT == 2 ? 16 : RT == 1 ? 8 : 4;  // values per 16-byte chunk
     constexpr int F = VPC / 4;  // float32 chunks per chunk (re-rank)
+    constexpr int R = 32 / G;   // rows per slab (one per group of G lanes)
+    constexpr int RP = 2 * R;   // rows per step (two slabs)
     static_assert(!RR || RT != 0, "float32 rows need no re-rank");
+    static_assert((G == 32 || (U == 1 && (G == 16 || G == 8))), "groups of 8 or 16 lanes take rows of one round");
     CandKnnArgs a = a0;
     if (a.rec != nullptr) {
         a.Q = a.rec->Q;
@@ -2390,7 +2393,9 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
     const int nchunk = RT == 2 ? int(a.row_bytes / 16u) - 1 : a.dpad / VPC;
     const int rstride = RT == 2 ? nchunk + 1 : nchunk;
     const uint4 *Xb = reinterpret_cast<const uint4 *>(a.rows);
-    uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * cb_ring_chunks(nchunk, VPC, RR);
+    uint4 *wring = reinterpret_cast<uint4 *>(cbsm) + size_t(warp) * cb_ring_chunks(nchunk, VPC, RR, RP);
+    const int cl = G == 32 ? lane : (lane & (G - 1));  // this lane's chunk of its rows
+    const int grp = G == 32 ? 0 : lane / G;            // this lane's row of a slab
     const uint32_t wring_s = smem_u32(wring);
     const int k = a.k;  // survivors kept (k + margin when re-ranking)
     const uint32_t n_items = *a.n_items;
@@ -2419,7 +2424,7 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
             const float *qrow = a.Q + qi * a.d;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int cc = lane + 32 * u;
+                const int cc = cl + 32 * u;
                 if (qvec && cc < nchunk && cc * VPC < a.d) {
 #pragma unroll
                     for (int h = 0; h < VPC / 4; ++h) {
@@ -2443,34 +2448,41 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
         // ids of rows [32 blk, 32 blk + 32) of the item, one per lane
         int blk = 0;
         int32_t ids = lane < c ? __ldg(clist + lane) : 0;
-        auto id_of = [&](int r) -> int32_t {
+        auto load_blk = [&](int r) {  // r warp-uniform
             if ((r >> 5) != blk) {
                 blk = r >> 5;
                 const int rr = 32 * blk + lane;
                 ids = rr < c ? __ldg(clist + rr) : 0;
             }
-            return __shfl_sync(0xffffffffu, ids, r & 31);
         };
-        // copy pair p (rows 2p and 2p + 1; an odd item's last row twice) into
-        // slot p % CB_SLOTS, one commit group per pair (empty past the item's
-        // last pair), and load an e4m3 pair's scales into sc.  Rounds
-        // u < U - 1 are always inside the row (32 (U - 1) < nchunk), only the
-        // last one needs a bound.
-        auto issue_pair = [&](int p, int slot, float2 &sc) {
-            if (2 * p < c) {
-                const int32_t id0 = id_of(2 * p);
-                const int32_t id1 = 2 * p + 1 < c ? id_of(2 * p + 1) : id0;
-                const uint4 *s0 = Xb + int64_t(id0) * rstride + lane;
-                const uint4 *s1 = Xb + int64_t(id1) * rstride + lane;
+        // step p covers rows RP p .. RP p + RP - 1: slab s (0, 1) of it is
+        // rows RP p + s R + g, row g of the slab on lane group g.  Each lane
+        // copies its chunks of its two rows into slot p % CB_SLOTS (one
+        // commit group per step, empty past the item's last step) and loads
+        // an e4m3 row's scale.  A row past the item repeats the step's first
+        // row (copied, never inserted).  Rounds u < U - 1 are always inside
+        // the row (32 (U - 1) < nchunk), only the last one needs a bound.
+        auto issue_step = [&](int p, int slot, float2 &sc) {
+            const int r0 = RP * p;
+            if (r0 < c) {
+                load_blk(r0);  // RP divides 32: the step's rows share a block
+                const int32_t first = __shfl_sync(0xffffffffu, ids, r0 & 31);
+                const int ra = r0 + grp, rb = r0 + R + grp;
+                int32_t id0 = __shfl_sync(0xffffffffu, ids, ra & 31);
+                int32_t id1 = __shfl_sync(0xffffffffu, ids, rb & 31);
+                id0 = ra < c ? id0 : first;
+                id1 = rb < c ? id1 : first;
+                const uint4 *s0 = Xb + int64_t(id0) * rstride + cl;
+                const uint4 *s1 = Xb + int64_t(id1) * rstride + cl;
                 if (RT == 2) {
                     sc.x = __ldg(reinterpret_cast<const float *>(Xb + int64_t(id0) * rstride + nchunk));
                     sc.y = __ldg(reinterpret_cast<const float *>(Xb + int64_t(id1) * rstride + nchunk));
                 }
-                const uint32_t d0 = wring_s + uint32_t(slot * 2 * nchunk + lane) * 16u;
-                const uint32_t d1 = d0 + uint32_t(nchunk) * 16u;
+                const uint32_t d0 = wring_s + uint32_t((slot * RP + grp) * nchunk + cl) * 16u;
+                const uint32_t d1 = d0 + uint32_t(R * nchunk) * 16u;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    if (u < U - 1 || lane + 32 * u < nchunk) {
+                    if (u < U - 1 || cl + 32 * u < nchunk) {
                         cp_async16_zfill(d0 + uint32_t(32 * u) * 16u, s0 + 32 * u, 16u);
                         cp_async16_zfill(d1 + uint32_t(32 * u) * 16u, s1 + 32 * u, 16u);
                     }
@@ -2480,24 +2492,24 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
         };
         WarpTopK<KR> top;
         top.init();
-        const int npairs = (c + 1) >> 1;
-        int s_issue = 0, s_use = 0;  // slots of the next pair to copy and to use
-        // scales of the pairs in flight (e4m3): scs[j] for pair p + j
+        const int nsteps = (c + RP - 1) / RP;
+        int s_issue = 0, s_use = 0;  // slots of the next step to copy and to use
+        // scales of the steps in flight (e4m3): scs[j] for step p + j
         float2 scs[CB_SLOTS];
 #pragma unroll
         for (int j = 0; j < CB_SLOTS; ++j) scs[j] = make_float2(1.f, 1.f);
 #pragma unroll
         for (int p = 0; p < CB_SLOTS - 1; ++p) {
-            issue_pair(p, s_issue, scs[p]);
+            issue_step(p, s_issue, scs[p]);
             s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
         }
-        for (int p = 0; p < npairs; ++p) {
-            issue_pair(p + CB_SLOTS - 1, s_issue, scs[CB_SLOTS - 1]);
+        for (int p = 0; p < nsteps; ++p) {
+            issue_step(p + CB_SLOTS - 1, s_issue, scs[CB_SLOTS - 1]);
             s_issue = s_issue + 1 == CB_SLOTS ? 0 : s_issue + 1;
-            // this thread's copies of pair p are in (groups of later pairs may not be)
+            // this thread's copies of step p are in (groups of later steps may not be)
             asm volatile("cp.async.wait_group %0;" ::"n"(CB_SLOTS - 1) : "memory");
-            const uint4 *r0 = wring + (s_use * 2) * nchunk + lane;
-            const uint4 *r1 = r0 + nchunk;
+            const uint4 *r0 = wring + (s_use * RP + grp) * nchunk + cl;
+            const uint4 *r1 = r0 + R * nchunk;
             s_use = s_use + 1 == CB_SLOTS ? 0 : s_use + 1;
             float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
             const float2 ns0 = make_float2(-scs[0].x, -scs[0].x), ns1 = make_float2(-scs[0].y, -scs[0].y);
@@ -2505,7 +2517,7 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
             for (int j = 0; j + 1 < CB_SLOTS; ++j) scs[j] = scs[j + 1];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const bool in = u < U - 1 || lane + 32 * u < nchunk;
+                const bool in = u < U - 1 || cl + 32 * u < nchunk;
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 const uint4 x0 = in ? r0[32 * u] : z;
                 const uint4 x1 = in ? r1[32 * u] : z;
@@ -2517,10 +2529,24 @@ __global__ void __launch_bounds__(CB_WARPS * 32, cb_min_blocks(KR)) k_cand_knn_r
                     a1 = chunk_sq_acc(x1, qv[u], a1);
                 }
             }
-            float d0, d1;
-            warp_sum2(a0.x + a0.y, a1.x + a1.y, lane, d0, d1);
-            top.insert(d0, id_of(2 * p), k, lane);
-            if (2 * p + 1 < c) top.insert(d1, id_of(2 * p + 1), k, lane);
+            // both slabs' sums over each group of G lanes: after one exchange
+            // the lower half of a group reduces slab 0, the upper half slab 1
+            // (with G = 32 the order of warp_sum2)
+            const bool hi = (lane & (G / 2)) != 0;
+            float part = hi ? a1.x + a1.y : a0.x + a0.y;
+            part += __shfl_xor_sync(0xffffffffu, hi ? a0.x + a0.y : a1.x + a1.y, G / 2);
+#pragma unroll
+            for (int o = G / 4; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            // row RP p + r is row g = r % R of slab s = r / R: its sum is on
+            // lane g G + s G / 2 (the ids of a later step may have replaced
+            // this step's block)
+            load_blk(RP * p);
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                const float dr = __shfl_sync(0xffffffffu, part, (r % R) * G + (r / R) * (G / 2));
+                const int row = RP * p + r;
+                if (row < c) top.insert(dr, __shfl_sync(0xffffffffu, ids, row & 31), k, lane);
+            }
         }
         cp_async_wait_all();  // no copy of this item outlives it
         bool finish = nch == 1;
@@ -2945,39 +2971,42 @@ cudaError_t launch_cand_knn(const mrpt_index *idx, const QueryLaunch &ql, cudaSt
     cudaError_t e;
     // rows of at least 8 16-byte chunks of values (float32 dpad >= 32,
     // bfloat16 dpad >= 64, e4m3 dpad > 112) and dpad <= 1024: each lane
-    // copies its own chunks (k_cand_knn_rows; with fewer than 32 chunks per
-    // row the lanes past them idle)
+    // copies its own chunks (k_cand_knn_rows); rows of at most 16 chunks go
+    // to groups of 16 or 8 lanes, two or four rows per slab
     const int vpc = RK == 2 ? 16 : RK == 1 ? 8 : 4;
     const int nchunk = RK == 2 ? int(row_bytes / 16) - 1 : idx->dpad / vpc;
     if (nchunk >= 8 && idx->dpad <= 1024) {
         const int U = (nchunk + 31) / 32;
+        const int G = nchunk <= 8 ? 8 : nchunk <= 16 ? 16 : 32;
         const void *kern = nullptr;
+#define ROWS_KERN(U_, RT_, RR_, G_) reinterpret_cast<const void *>(k_cand_knn_rows<KR, U_, RT_, RR_, G_>)
         if (RK == 2) {
-            kern = U == 1 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 2, true>)
-                          : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 2, true>);
+            kern = G == 8 ? ROWS_KERN(1, 2, true, 8) : G == 16 ? ROWS_KERN(1, 2, true, 16)
+                   : U == 1 ? ROWS_KERN(1, 2, true, 32) : ROWS_KERN(2, 2, true, 32);
         } else if (RK == 1 && rerank) {
-            kern = U == 1   ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 1, true>)
-                   : U == 2 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 1, true>)
-                   : U == 3 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 1, true>)
-                            : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 1, true>);
+            kern = G == 8    ? ROWS_KERN(1, 1, true, 8)
+                   : G == 16 ? ROWS_KERN(1, 1, true, 16)
+                   : U == 1  ? ROWS_KERN(1, 1, true, 32)
+                   : U == 2  ? ROWS_KERN(2, 1, true, 32)
+                   : U == 3  ? ROWS_KERN(3, 1, true, 32)
+                             : ROWS_KERN(4, 1, true, 32);
         } else if (RK == 1) {
-            kern = U == 1   ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 1, false>)
-                   : U == 2 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 1, false>)
-                   : U == 3 ? reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 1, false>)
-                            : reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 1, false>);
+            kern = G == 8    ? ROWS_KERN(1, 1, false, 8)
+                   : G == 16 ? ROWS_KERN(1, 1, false, 16)
+                   : U == 1  ? ROWS_KERN(1, 1, false, 32)
+                   : U == 2  ? ROWS_KERN(2, 1, false, 32)
+                   : U == 3  ? ROWS_KERN(3, 1, false, 32)
+                             : ROWS_KERN(4, 1, false, 32);
         } else {
-            const void *by_u[8] = {
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 1, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 2, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 3, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 4, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 5, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 6, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 7, 0, false>),
-                reinterpret_cast<const void *>(k_cand_knn_rows<KR, 8, 0, false>)};
-            kern = by_u[U - 1];
+            const void *by_u[8] = {ROWS_KERN(1, 0, false, 32), ROWS_KERN(2, 0, false, 32),
+                                   ROWS_KERN(3, 0, false, 32), ROWS_KERN(4, 0, false, 32),
+                                   ROWS_KERN(5, 0, false, 32), ROWS_KERN(6, 0, false, 32),
+                                   ROWS_KERN(7, 0, false, 32), ROWS_KERN(8, 0, false, 32)};
+            kern = G == 8 ? ROWS_KERN(1, 0, false, 8) : G == 16 ? ROWS_KERN(1, 0, false, 16) : by_u[U - 1];
         }
-        const size_t smem = size_t(CB_WARPS) * size_t(cb_ring_chunks(nchunk, vpc, rerank)) * 16;
+#undef ROWS_KERN
+        const int rows = 2 * (32 / G);
+        const size_t smem = size_t(CB_WARPS) * size_t(cb_ring_chunks(nchunk, vpc, rerank, rows)) * 16;
         e = launch_shape(kern, CB_WARPS * 32, smem, idx->device, &per_sm, &sms);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(

@@ -87,3 +87,29 @@ def check_lowp_results(X, Q, gi, gd, oi, od, cand_sets, min_recall):
     rec = hit / max(total, 1)
     assert rec >= min_recall, f"tie-aware recall {rec:.4f} below {min_recall}"
     return rec
+
+
+def emulated_recall(X, Q, sets, oi, od, k, margin, prec):
+    """Tie-aware recall of a float64 emulation of a reduced-precision screen
+    (prec 1 bfloat16, 2 e4m3 with the per-row scale): the k + margin members
+    of S nearest by the reduced copy's distances, re-ranked exactly, the k
+    nearest kept."""
+    import torch
+    import bench
+    Xl = bench.lowp_copy(torch.from_numpy(X), prec, torch).numpy()
+    hit = total = 0
+    for i, s in enumerate(sets):
+        ids = np.array(sorted(s), dtype=np.int64)
+        q = Q[i].astype(np.float64)
+        screen = ((Xl[ids] - q) ** 2).sum(1)
+        keep = ids[np.lexsort((ids, screen))[:k + margin]]
+        exact = ((X[keep].astype(np.float64) - q) ** 2).sum(1)
+        best = keep[np.lexsort((keep, exact))[:k]]
+        fin = np.isfinite(od[i])
+        if not fin.any():
+            continue
+        kth = od[i][fin][-1]
+        dist = np.sqrt(((X[best].astype(np.float64) - q) ** 2).sum(1))
+        hit += min(int((dist <= kth * (1 + 1e-6)).sum()), int(fin.sum()))
+        total += int(fin.sum())
+    return hit / total

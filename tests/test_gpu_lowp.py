@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads
-from _parity import REL_TOL, check_results, oracle_sets
+from _parity import REL_TOL, check_results, emulated_recall, oracle_sets
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -161,30 +161,6 @@ def test_large_candidate_sets_float32_match_oracle(mr):
     idx.close()
 
 
-def _emulated_recall(X, Q, sets, oi, od, k, margin):
-    """Tie-aware recall of a float64 emulation of the e4m3 screen: the
-    k + margin members of S nearest by the e4m3 copy's distances, re-ranked
-    exactly, the k nearest kept."""
-    import bench
-    Xl = bench.lowp_copy(torch.from_numpy(X), 2, torch).numpy()
-    hit = total = 0
-    for i, s in enumerate(sets):
-        ids = np.array(sorted(s), dtype=np.int64)
-        q = Q[i].astype(np.float64)
-        screen = ((Xl[ids] - q) ** 2).sum(1)
-        keep = ids[np.lexsort((ids, screen))[:k + margin]]
-        exact = ((X[keep].astype(np.float64) - q) ** 2).sum(1)
-        best = keep[np.lexsort((keep, exact))[:k]]
-        fin = np.isfinite(od[i])
-        if not fin.any():
-            continue
-        kth = od[i][fin][-1]
-        dist = np.sqrt(((X[best].astype(np.float64) - q) ** 2).sum(1))
-        hit += min(int((dist <= kth * (1 + 1e-6)).sum()), int(fin.sum()))
-        total += int(fin.sum())
-    return hit / total
-
-
 @pytest.mark.parametrize("d,k,margin", [(200, 10, 16), (520, 40, 24), (1000, 100, 32)],
                          ids=["d200-k10", "d520-k40", "d1000-k100"])
 def test_fp8_rows_of_one_and_two_rounds(mr, d, k, margin):
@@ -210,6 +186,6 @@ def test_fp8_rows_of_one_and_two_rounds(mr, d, k, margin):
     assert np.array_equal(dbg["n_cand"].cpu().numpy(), oncand)
     assert oncand.min() > 600
     sets = oracle_sets(ref, oleaf, v)
-    floor = _emulated_recall(X, Q, sets, oi, od, k, margin) - 0.02
+    floor = emulated_recall(X, Q, sets, oi, od, k, margin, 2) - 0.02
     check_lowp_results(X, Q, ids.cpu().numpy(), dd.cpu().numpy(), oi, od, sets, floor)
     idx.close()
