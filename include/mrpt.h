@@ -173,7 +173,21 @@ typedef struct mrpt_query_opts {
      * from CUDA events recorded on the index's stream; the call then
      * synchronises */
     float *stage_ms;
+    /* path 0: how a query's votes are counted (Sec. III-A: F(x;q) for the
+     * points of its T leaves).  0 (default): 8-bit counters in shared memory
+     * for n <= 65,536, else a hash table when the T leaves of a query hold at
+     * most MRPT_VOTE_HASH_ENTRIES entries, else counters over 65,536-id
+     * chunks, one pass per chunk.  1: counters (over id chunks when n >
+     * 65,536).  2: the hash table; INVALID_ARG when n_trees * ceil(n / 2^l)
+     * exceeds MRPT_VOTE_HASH_ENTRIES or n >= 2^24.  Same results. */
+    int32_t vote_table;
 } mrpt_query_opts;
+
+#define MRPT_VOTE_COUNTERS 1
+#define MRPT_VOTE_HASH 2
+/* entries of a query's T leaves the hash table takes: 3/4 of its 32,768
+ * slots, so the table never fills */
+#define MRPT_VOTE_HASH_ENTRIES 24576
 
 int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t v,
                   const mrpt_query_opts *opts, int32_t *out_ids, float *out_dists);

@@ -59,6 +59,9 @@ MRPT_SPARSITY_FIXED = 1
 MRPT_PREC_FP32 = 0
 MRPT_PREC_BF16 = 1
 MRPT_PREC_FP8 = 2
+MRPT_VOTE_COUNTERS = 1
+MRPT_VOTE_HASH = 2
+MRPT_VOTE_HASH_ENTRIES = 24576
 MRPT_NOALLOC_MAX_LEAF_ENTRIES = 1048512
 
 
@@ -87,6 +90,7 @@ class QueryOpts(ctypes.Structure):
         ("cand", ctypes.c_void_p),
         ("cand_cap", ctypes.c_int64),
         ("stage_ms", ctypes.POINTER(ctypes.c_float)),
+        ("vote_table", ctypes.c_int32),
     ]
 
 
@@ -389,13 +393,14 @@ def mrpt_info(index: Index) -> IndexInfo:
 def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=None,
                   out_dists=None, debug: bool = False, cand_cap: int | None = None,
                   stage_ms=None, path: int = 0, precision: int = 0, margin: int = 0,
-                  chunk: int = 0, ring: int = 0, n_cand_out=None):
+                  chunk: int = 0, ring: int = 0, n_cand_out=None, vote_table: int = 0):
     """Algorithm 4 for the rows of Q.  Outputs live where Q lives (device
     tensors for a CUDA tensor, numpy arrays for host input) unless given.
     With ``debug`` also returns a dict of the internals: proj, leaf, votes,
     n_cand and cand (members of S, row padded).  ``n_cand_out`` (m int64,
     device or host) receives |S| of every query on its own, without the
-    m x n debug buffers.  ``stage_ms`` (a float32
+    m x n debug buffers.  ``vote_table`` picks how votes are counted (0
+    automatic, MRPT_VOTE_COUNTERS, MRPT_VOTE_HASH; see mrpt.h).  ``stage_ms`` (a float32
     numpy array of 4) receives the routing, voting, candidate-search and
     total device times of this call in ms.  ``path`` 0 runs the vote/emit
     and candidate-search kernels, 1 the fused kernel.  ``precision``
@@ -420,6 +425,7 @@ def mrpt_query_ex(index: Index, Q, k: int, v: int, n_trees: int = 0, out_ids=Non
     opts.margin = int(margin)
     opts.chunk = int(chunk)
     opts.ring = int(ring)
+    opts.vote_table = int(vote_table)
     if stage_ms is not None:
         assert stage_ms.dtype == np.float32 and stage_ms.size >= 4
         opts.stage_ms = stage_ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
@@ -575,12 +581,13 @@ class Plan:
     options, any batch of up to m_max queries per run."""
 
     def __init__(self, index: Index, m_max: int, k: int, v: int, n_trees: int = 0, path: int = 0,
-                 precision: int = 0, margin: int = 0, chunk: int = 0, ring: int = 0):
+                 precision: int = 0, margin: int = 0, chunk: int = 0, ring: int = 0, vote_table: int = 0):
         self._lib = load_library()
         self.index, self.m_max, self.k, self.v = index, m_max, k, v
         opts = QueryOpts()
         opts.n_trees, opts.path, opts.precision = int(n_trees), int(path), int(precision)
         opts.margin, opts.chunk, opts.ring = int(margin), int(chunk), int(ring)
+        opts.vote_table = int(vote_table)
         h = ctypes.c_void_p()
         _check(self._lib.mrpt_plan_create(index.handle, int(m_max), int(k), int(v),
                                           ctypes.byref(opts), ctypes.byref(h)))

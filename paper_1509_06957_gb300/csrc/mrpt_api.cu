@@ -413,6 +413,14 @@ int mrpt_info(const mrpt_index *idx, mrpt_index_info *info) {
     return MRPT_OK;
 }
 
+// A vote-table choice the index can take (mrpt_query_opts.vote_table).
+static bool vote_table_ok(const mrpt_index *idx, int32_t n_trees, int32_t vt) {
+    if (vt == 0 || vt == MRPT_VOTE_COUNTERS) return true;
+    if (vt != MRPT_VOTE_HASH) return false;
+    const int64_t leaf_max = (idx->n + idx->L - 1) / idx->L;
+    return int64_t(n_trees) * leaf_max <= MRPT_VOTE_HASH_ENTRIES && idx->n < (int64_t(1) << 24);
+}
+
 // Host queries in batches of at least this many are copied in chunks, each
 // chunk routed as soon as it has arrived, so the copy overlaps routing.
 constexpr int kPipeChunks = 4;
@@ -434,6 +442,11 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
     }
     if (opts && (opts->chunk < 0 || opts->ring < 0)) {
         set_error("mrpt_query: chunk and ring must be >= 0");
+        return MRPT_ERR_INVALID_ARG;
+    }
+    if (opts && !vote_table_ok(idx, n_trees, opts->vote_table)) {
+        set_error("mrpt_query: vote_table must be 0, 1 or 2, and 2 needs n_trees * ceil(n / 2^l) <= " +
+                  std::to_string(MRPT_VOTE_HASH_ENTRIES) + " and n < 2^24");
         return MRPT_ERR_INVALID_ARG;
     }
     if (opts && opts->cand && opts->cand_cap < 0) {
@@ -539,6 +552,7 @@ int mrpt_query_ex(mrpt_index *idx, const float *Q, int64_t m, int32_t k, int32_t
     ql.path = opts ? opts->path : 0;
     ql.precision = precision;
     ql.margin = margin;
+    ql.vote_table = opts ? opts->vote_table : 0;
     // two-kernel path: candidate lists for mb queries at a time, mb = m
     // unless their scratch would pass kCandScratchBudget
     int64_t mb = m;
@@ -659,7 +673,8 @@ int mrpt_plan_create(mrpt_index *idx, int64_t m_max, int32_t k, int32_t v,
         (precision == MRPT_PREC_BF16 && !idx->Xb) || (precision == MRPT_PREC_FP8 && !idx->X8) ||
         (precision != MRPT_PREC_FP32 && (path != 0 || margin < 0 || k + margin > MRPT_MAX_K)) ||
         (opts && (opts->chunk < 0 || opts->ring < 0 || opts->proj || opts->leaf || opts->votes ||
-                  opts->n_cand || opts->cand || opts->stage_ms))) {
+                  opts->n_cand || opts->cand || opts->stage_ms)) ||
+        (opts && !vote_table_ok(idx, n_trees, opts->vote_table))) {
         set_error("mrpt_plan_create: invalid argument (need m_max >= 1, 1 <= k <= " +
                   std::to_string(MRPT_MAX_K) +
                   ", 1 <= v <= n_trees <= T, a valid path/precision, no debug outputs)");
@@ -708,6 +723,7 @@ int mrpt_plan_create(mrpt_index *idx, int64_t m_max, int32_t k, int32_t v,
     ql.path = path;
     ql.precision = precision;
     ql.margin = margin;
+    ql.vote_table = opts ? opts->vote_table : 0;
     if (path == 0) cand_carve(lay, cand_base, m_max, ql);
     ql.counters = plan->counters;
     ql.rec = plan->rec;

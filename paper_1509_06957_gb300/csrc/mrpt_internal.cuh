@@ -207,6 +207,7 @@ struct QueryLaunch {
     int32_t precision;     // 0 float32 rows, 1 bfloat16 rows + float32 re-rank
     int32_t margin;        // survivors beyond k kept for the re-rank
     int32_t ring;          // candidate rows staged per search warp (0 = auto)
+    int32_t vote_table;    // path 0: 0 auto, MRPT_VOTE_COUNTERS, MRPT_VOTE_HASH
     uint32_t *counters;    // 8 work-counter words ([0] unused); null = the index's
     cudaStream_t stream;   // stream of the launches (plans capture on their own)
     bool use_stream;       // take `stream` instead of the index's stream

@@ -1627,6 +1627,113 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
     }
 }
 
+// Hashed vote counters (n > 65,536 with every query's T leaves holding at
+// most VH_SLOTS * 3 / 4 entries): one pass per query, no id chunks.  The
+// table is VH_SLOTS 32-bit words in shared memory, a word (id + 1) << 8 |
+// count, 0 when empty; an id's slot is found by a multiplicative hash and
+// linear probing.  The T leaves hold at most 3/4 VH_SLOTS entries, so at
+// most that many distinct ids: the table never fills.  An id claims an empty
+// slot with a compare-and-swap (count 1); a later vote adds 1 to the word, and
+// the old count tells when it went from v - 1 to v (Algorithm 4: the id
+// enters S).  T <= 255 votes fit the 8-bit count.
+constexpr int VH_LOG = 15;
+constexpr int VH_SLOTS = 1 << VH_LOG;  // 128 KB of shared memory
+constexpr int VH_THREADS = 1024;
+constexpr int VH_WARPS = VH_THREADS / 32;
+
+__device__ __forceinline__ bool vote_hash(uint32_t *tab, int32_t id, uint32_t vm1) {
+    const uint32_t tag = (uint32_t(id) + 1u) << 8;
+    uint32_t h = (uint32_t(id) * 0x9E3779B1u) >> (32 - VH_LOG);
+    for (int probe = 0; probe < VH_SLOTS; ++probe) {
+        uint32_t w = tab[h];
+        if (w == 0u) {
+            w = atomicCAS(tab + h, 0u, tag | 1u);
+            if (w == 0u) return vm1 == 0u;
+        }
+        if ((w & 0xffffff00u) == tag) return (atomicAdd(tab + h, 1u) & 0xffu) == vm1;
+        h = (h + 1u) & uint32_t(VH_SLOTS - 1);
+    }
+    return false;  // not reached: the table holds every distinct id of the query
+}
+
+// Per query (one block of 32 warps, queries taken from an atomic counter):
+// clear the table; window i (128 entries: one 16-byte load per lane from
+// the leaf's 16-byte-aligned start) is window i % K of tree i / K, K the
+// windows of the longest leaf (leaf sizes differ by at most one); warps take
+// windows w, w + 32, ...; every entry in its tree's segment votes.
+__global__ void __launch_bounds__(VH_THREADS, 1) k_vote_hash(const VoteEmitArgs a0) {
+    VoteEmitArgs a = a0;
+    if (a.rec != nullptr) a.m = a.rec->m;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem);           // VH_SLOTS words
+    int64_t *tg4 = reinterpret_cast<int64_t *>(tab + VH_SLOTS);    // per tree: aligned int4 start
+    int2 *tlh = reinterpret_cast<int2 *>(tg4 + a.T_use);           // per tree: (length, head)
+    __shared__ int64_t s_q;
+    __shared__ int s_cnt;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const uint32_t vm1 = uint32_t(a.v - 1);
+    const int T = a.T_use;
+    const int K = a.win;  // windows per tree
+    const int W = T * K;
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(a.work, 1u);
+            s_q = int64_t(w) < a.m ? int64_t(w) : -1;
+            s_cnt = 0;
+        }
+        {
+            uint4 *t4 = reinterpret_cast<uint4 *>(tab);
+            for (int w = tid; w < VH_SLOTS / 4; w += VH_THREADS) t4[w] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi < 0) break;
+        for (int t = tid; t < T; t += VH_THREADS) {
+            const int32_t lf = a.leaf_of_q[qi * T + t];
+            const int32_t p = a.leaf_off[lf], e = a.leaf_off[lf + 1];
+            const int64_t g = int64_t(t) * a.n + p;
+            const int32_t head = int32_t(g & 3);
+            tg4[t] = (g - head) >> 2;
+            tlh[t] = make_int2(e - p, head);
+        }
+        __syncthreads();
+        int32_t *clist = a.cand + qi * int64_t(a.capq);
+        for (int i = warp; i < W; i += VH_WARPS) {
+            const int t = i / K;
+            const int j = i - t * K;
+            const int2 lh = tlh[t];
+            const int32_t rel = 4 * (32 * j + lane) - lh.y;  // segment position of the lane's first entry
+            const uint32_t ok = rel + 3 >= 0 && rel < lh.x;
+            const int4 q = ldg4_if(reinterpret_cast<const int4 *>(a.leaf_ids) + tg4[t] + 32 * j + lane, ok);
+            if (ok) {
+                const int32_t e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (rel + u >= 0 && rel + u < lh.x && vote_hash(tab, e[u], vm1)) {
+                        const int slot = atomicAdd(&s_cnt, 1);
+                        if (slot < a.capq) clist[slot] = e[u];
+                        if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = e[u];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every vote of this query is in
+        if (a.dbg_votes != nullptr) {
+            uint8_t *row = a.dbg_votes + qi * a.n;
+            for (int64_t x = tid; x < a.n; x += VH_THREADS) row[x] = 0;
+            __syncthreads();
+            for (int h = tid; h < VH_SLOTS; h += VH_THREADS) {
+                const uint32_t w = tab[h];
+                if (w != 0u) row[(w >> 8) - 1u] = uint8_t(w & 0xffu);
+            }
+        }
+        if (tid == 0) publish_items(a, qi, s_cnt);
+        __syncthreads();  // the table and s_cnt are reused by the next query
+    }
+}
+
 // One lane's four entries e.x..e.w of a vote window: each adds one vote to
 // its 8-bit counter (byte id & 3 of word id >> 2 at shared address cnt_s);
 // with ok == 0 the four votes go to the lane's own spare word at shared
@@ -2873,6 +2980,46 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     // ceil(size / 4) (the vote layout pads with the sentinel)
     const int64_t min_units = (idx->n / idx->L + 3) / 4;
     const bool one = flat && (idx->vote_win + 1) / 2 <= 1 && min_units >= 32;
+    // hashed counters when the T leaves of a query hold at most 3/4 of the
+    // table (one pass instead of one per 65,536-id chunk); ids + 1 take 24 bits
+    static_assert(MRPT_VOTE_HASH_ENTRIES <= VH_SLOTS * 3 / 4, "the hash table must not fill");
+    const bool fits = int64_t(ql.n_trees) * leaf_len <= MRPT_VOTE_HASH_ENTRIES && idx->n < (int64_t(1) << 24);
+    const bool hashed = ql.vote_table == MRPT_VOTE_HASH || (ql.vote_table == 0 && !flat && fits);
+    if (hashed) {
+        VoteEmitArgs h{};
+        h.n = idx->n;
+        h.leaf_of_q = ql.leaf;
+        h.T_use = ql.n_trees;
+        h.leaf_off = idx->leaf_off;
+        h.leaf_ids = idx->leaf_ids;
+        h.m = ql.m;
+        h.v = ql.v;
+        h.cand = ql.cand_list;
+        h.capq = ql.capq;
+        h.ncand = ql.ncand;
+        uint32_t *hc = ql.counters ? ql.counters : idx->status;
+        h.work = hc + 1;
+        h.rec = ql.rec;
+        h.items = ql.items;
+        h.n_items = hc + 5;
+        h.chunk = ql.chunk;
+        h.done = ql.done;
+        h.dbg_votes = ql.votes;
+        h.dbg_ncand = ql.n_cand;
+        h.dbg_cand = ql.cand;
+        h.cand_cap = ql.cand_cap;
+        // 128-entry windows of the longest leaf, whose start lies up to 3
+        // entries past a 16-byte boundary
+        h.win = int((leaf_len + 3 + VE_WIN - 1) / VE_WIN);
+        const size_t hsmem = size_t(VH_SLOTS) * 4 + size_t(ql.n_trees) * 16;
+        int hper = 0, hsms = 0;
+        cudaError_t he = launch_shape(reinterpret_cast<const void *>(k_vote_hash), VH_THREADS, hsmem, idx->device,
+                                      &hper, &hsms);
+        if (he != cudaSuccess) return he;
+        const int64_t hblocks = std::max<int64_t>(1, std::min<int64_t>(ql.m, int64_t(hsms) * std::max(hper, 1)));
+        k_vote_hash<<<unsigned(hblocks), VH_THREADS, hsmem, s>>>(h);
+        return cudaGetLastError();
+    }
     auto kern = flat ? (one ? k_vote_flat<true> : k_vote_flat<false>) : packed ? k_vote_packed : k_vote_emit;
     const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 8
                         : packed ? size_t(cnt_words + 32) * 4 + size_t(4 * ql.n_trees + 1) * 4

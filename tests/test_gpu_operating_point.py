@@ -106,16 +106,18 @@ def test_internals_over_a_large_batch(mr, bench_case, path):
                   c["od"][:m], oracle_sets(c["ref"], c["oleaf"][:m], V))
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path,vote_table", [(1, 0), (0, 1), (0, 2)], ids=["fused", "counters", "hash"])
 @pytest.mark.parametrize("l", [9, 12])
-def test_chunked_votes_over_a_large_batch(mr, l, path):
-    """n = 140,000 (counters in three id chunks): depth 9 takes per-tree
-    windows (k_vote_emit), depth 12 the packed segments (k_vote_packed)."""
+def test_chunked_votes_over_a_large_batch(mr, l, path, vote_table):
+    """n = 140,000 over 2,000 queries (many per block): counters in three id
+    chunks, depth 9 with per-tree windows (k_vote_emit) and depth 12 with the
+    packed segments (k_vote_packed); the hash table (k_vote_hash); and the
+    fused kernel's own chunks."""
     n, d, m, T_, v, k = 140000, 8, 2000, 20, 3, 10
     X, Q = workloads.gaussian_mixture(n, d, m, n_centres=30, seed=14)
     idx = mr.mrpt_build(torch.from_numpy(X).cuda(), T_, l, 0.5, 4)
     ids, dists, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), k, v, debug=True,
-                                       cand_cap=2048, path=path)
+                                       cand_cap=2048, path=path, vote_table=vote_table)
     torch.cuda.synchronize()
     ref = oracle.grow_trees(X, T_, l, 0.5, 4)
     assert np.array_equal(mr.mrpt_export(idx, "LEAF_IDS"), ref.leaf_ids)

@@ -27,21 +27,22 @@ def _dens(d):
     return float(np.float32(1.0 / np.sqrt(d)))
 
 
-def _run(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0):
+def _run(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0, vote_table=0):
     dev = torch.device("cuda:0")
     if host:
         idx = mr.mrpt_build(X, T, l, density, seed)
-        ids, dists, dbg = mr.mrpt_query_ex(idx, Q, k, v, n_trees=n_trees, debug=True, path=path)
+        ids, dists, dbg = mr.mrpt_query_ex(idx, Q, k, v, n_trees=n_trees, debug=True, path=path,
+                                           vote_table=vote_table)
         return idx, ids, dists, dbg
     idx = mr.mrpt_build(torch.from_numpy(X).to(dev), T, l, density, seed)
     ids, dists, dbg = mr.mrpt_query_ex(idx, torch.from_numpy(Q).to(dev), k, v, n_trees=n_trees,
-                                       debug=True, path=path)
+                                       debug=True, path=path, vote_table=vote_table)
     torch.cuda.synchronize()
     return idx, ids.cpu().numpy(), dists.cpu().numpy(), {kk: vv.cpu().numpy() for kk, vv in dbg.items()}
 
 
-def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0):
-    idx, gi, gd, dbg = _run(mr, X, Q, T, l, k, v, density, seed, n_trees, host, path)
+def _full_check(mr, X, Q, T, l, k, v, density, seed, n_trees=0, host=False, path=0, vote_table=0):
+    idx, gi, gd, dbg = _run(mr, X, Q, T, l, k, v, density, seed, n_trees, host, path, vote_table)
     ref = oracle.grow_trees(X, T, l, density, seed)
     check_index_parity(idx, mr, ref)
     Tq = n_trees or T
@@ -136,15 +137,45 @@ def test_vote_threshold_equal_to_T_and_subset_of_trees(mr):
     _full_check(mr, X, Q, 8, 4, 10, 3, _dens(32), 2, n_trees=5)
 
 
-@pytest.mark.parametrize("path", PATHS)
+# (path, vote table): the fused kernel's own id chunks, then path 0 with
+# counters over id chunks and with the hash table
+VOTE_MODES = [(1, 0), (0, 1), (0, 2)]
+
+
+@pytest.mark.parametrize("path,vote_table", VOTE_MODES, ids=["fused", "counters", "hash"])
 @pytest.mark.parametrize("l", [9, 12])
-def test_counter_chunks_beyond_shared_memory(mr, path, l):
-    """n > 65,536 ids: votes are counted in id chunks (per-tree cursors).
-    Depth 9 (leaves of 274, about 91 per chunk) takes per-tree windows;
-    depth 12 (leaves of 35, about 12 per chunk) takes windows over the
-    chunk's segments laid end to end."""
+def test_counter_chunks_beyond_shared_memory(mr, path, vote_table, l):
+    """n > 65,536 ids.  Counters: votes in id chunks (per-tree cursors); depth
+    9 (leaves of 274, about 91 per chunk) takes per-tree windows, depth 12
+    (leaves of 35, about 12 per chunk) windows over the chunk's segments laid
+    end to end.  Hash: one table of (id, count) words for the query's 6
+    leaves.  Votes, |S|, S and rows equal the oracle's."""
     X, Q = workloads.gaussian_mixture(140000, 8, 12, n_centres=30, seed=10)
-    _full_check(mr, X, Q, 6, l, 10, 2, 0.5, 4, path=path)
+    _full_check(mr, X, Q, 6, l, 10, 2, 0.5, 4, path=path, vote_table=vote_table)
+
+
+@pytest.mark.parametrize("v", [1, 3])
+def test_hashed_votes_full_table_load(mr, v):
+    """The hash table at its capacity: 96 trees of depth 9 over n = 131,072
+    hold 96 * 256 = 24,576 entries per query (3/4 of the table's slots), the
+    most it takes.  Votes, |S|, S and rows equal the oracle's at v = 1 and
+    3."""
+    X, Q = workloads.gaussian_mixture(131072, 8, 6, n_centres=30, seed=12)
+    _full_check(mr, X, Q, 96, 9, 10, v, 0.5, 6, vote_table=2)
+
+
+def test_hashed_votes_refused_beyond_capacity(mr):
+    """vote_table = 2 with more than 24,576 leaf entries per query is
+    refused before any work."""
+    X, Q = workloads.gaussian_mixture(131072, 8, 2, n_centres=30, seed=12)
+    idx = mr.mrpt_build(torch.from_numpy(X).cuda(), 97, 9, 0.5, 6)
+    with pytest.raises(mr.MRPTError) as e:
+        mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), 10, 2, vote_table=2)
+    assert e.value.code == mr.MRPT_ERR_INVALID_ARG
+    ids, _ = mr.mrpt_query_ex(idx, torch.from_numpy(Q).cuda(), 10, 2, n_trees=96, vote_table=2)
+    torch.cuda.synchronize()
+    assert ids.shape == (2, 10)
+    idx.close()
 
 
 def test_degenerate_all_equal_points(mr):
