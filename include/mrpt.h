@@ -174,12 +174,11 @@ typedef struct mrpt_query_opts {
      * synchronises */
     float *stage_ms;
     /* path 0: how a query's votes are counted (Sec. III-A: F(x;q) for the
-     * points of its T leaves).  0 (default): 8-bit counters in shared memory
-     * for n <= 65,536, else a hash table when the T leaves of a query hold at
-     * most MRPT_VOTE_HASH_ENTRIES entries, else counters over 65,536-id
-     * chunks, one pass per chunk.  1: counters (over id chunks when n >
-     * 65,536).  2: the hash table; INVALID_ARG when n_trees * ceil(n / 2^l)
-     * exceeds MRPT_VOTE_HASH_ENTRIES or n >= 2^24.  Same results. */
+     * points of its T leaves).  0 (default) and 1: 8-bit counters in shared
+     * memory, over 65,536-id chunks (one pass per chunk) when n > 65,536.
+     * 2: one pass over a hash table of (id, count) words in shared memory;
+     * INVALID_ARG when n_trees * ceil(n / 2^l) exceeds
+     * MRPT_VOTE_HASH_ENTRIES or n >= 2^24.  Same results. */
     int32_t vote_table;
 } mrpt_query_opts;
 

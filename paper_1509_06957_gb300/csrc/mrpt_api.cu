@@ -137,6 +137,7 @@ static void free_index(mrpt_index *idx) {
     cudaFree(idx->leaf_ids);
     cudaFree(idx->leaf4);
     cudaFree(idx->leaf_off4);
+    cudaFree(idx->chunk_bnd);
     cudaFree(idx->Xb);
     cudaFree(idx->X8);
     cudaFree(idx->status);

@@ -598,8 +598,49 @@ __global__ void k_bank_spread_windows(int32_t *__restrict__ leaf4, int32_t T,
 
 }  // namespace
 
+// Position of the first id >= c * VOTE_CHUNK_IDS in every leaf of every
+// tree (the leaf's ids ascend), for c = 0 .. C: one thread per (tree, leaf,
+// c), a binary search over the leaf.
+__global__ void k_chunk_bounds(const int32_t *__restrict__ leaf_ids, int64_t n, int32_t T,
+                               const int32_t *__restrict__ leaf_off, int64_t L, int32_t C,
+                               int32_t *__restrict__ bnd) {
+    const int64_t total = int64_t(T) * L * (C + 1);
+    for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < total;
+         x += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = int32_t(x % (C + 1));
+        const int64_t tj = x / (C + 1);
+        const int64_t j = tj % L;
+        const int64_t t = tj / L;
+        int32_t lo = leaf_off[j], hi = leaf_off[j + 1];
+        const int32_t *ids = leaf_ids + t * n;
+        const int64_t lim = int64_t(c) * VOTE_CHUNK_IDS;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (int64_t(ids[mid]) < lim)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        bnd[x] = lo;
+    }
+}
+
 int build_vote_layout(mrpt_index *idx) {
-    if (idx->n > VOTE_CHUNK_IDS) return MRPT_OK;
+    if (idx->n > VOTE_CHUNK_IDS) {
+        const int32_t C = int32_t((idx->n + VOTE_CHUNK_IDS - 1) / VOTE_CHUNK_IDS);
+        const int64_t total = int64_t(idx->T) * idx->L * (C + 1);
+        int rc;
+        if ((rc = dev_alloc((void **)&idx->chunk_bnd, size_t(total) * 4, "id-chunk bounds"))) return rc;
+        idx->device_bytes += total * 4;
+        idx->n_chunks = C;
+        const int blocks = int(std::min<int64_t>((total + 255) / 256, 152 * 32));
+        k_chunk_bounds<<<blocks, 256, 0, idx->stream>>>(idx->leaf_ids, idx->n, idx->T, idx->leaf_off, idx->L, C,
+                                                        idx->chunk_bnd);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "k_chunk_bounds");
+        return MRPT_OK;
+    }
     const int64_t L = idx->L;
     std::vector<int32_t> off(size_t(L + 1)), off4(size_t(L + 1));
     cudaError_t e = cudaMemcpy(off.data(), idx->leaf_off, size_t(L + 1) * 4, cudaMemcpyDeviceToHost);

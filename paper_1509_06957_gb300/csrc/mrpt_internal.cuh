@@ -87,6 +87,11 @@ struct mrpt_index {
     int32_t *leaf_off4 = nullptr; // L + 1
     int64_t vote_s4 = 0;          // int4s per tree
     int32_t vote_win = 0;         // 128-entry windows per leaf (the longest leaf)
+    // n > VOTE_CHUNK_IDS: per (tree t, leaf j) the position in tree t's
+    // leaf_ids row of the first id >= c * VOTE_CHUNK_IDS, c = 0 .. n_chunks
+    // (c = n_chunks: the leaf's end), at chunk_bnd[(t L + j)(n_chunks + 1) + c]
+    int32_t *chunk_bnd = nullptr;
+    int32_t n_chunks = 0;
     uint32_t *status = nullptr;  // [0] latched status bits, [1] work counter
 
     std::vector<int32_t> h_col_off, h_dim;
@@ -152,8 +157,8 @@ inline int32_t vote_cnt_words(int64_t n) {
 // real ones; it is never reported as a candidate).
 inline int32_t vote_sentinel(int64_t n) { return 4 * vote_cnt_words(n); }
 
-// Builds idx->leaf4 / leaf_off4 from idx->leaf_ids (no-op when n is above
-// VOTE_CHUNK_IDS).
+// Builds idx->leaf4 / leaf_off4 from idx->leaf_ids, or for n above
+// VOTE_CHUNK_IDS the id-chunk boundaries of every leaf (idx->chunk_bnd).
 int build_vote_layout(mrpt_index *idx);
 
 // Projections and median splits for every tree; fills idx->split,

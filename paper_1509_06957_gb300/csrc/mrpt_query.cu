@@ -842,6 +842,27 @@ __global__ void k_to_bf16(const float *__restrict__ X, __nv_bfloat16 *__restrict
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(lossy, 1u);
 }
 
+// End of tree t's ids below lim = (c + 1) * CH_IDS inside the query's leaf
+// lf of that tree (entries [lo, hi) of the tree's leaf_ids row, ids
+// ascending): one load from the index's id-chunk bounds when it has them,
+// else a binary search of the leaf.
+__device__ __forceinline__ int32_t chunk_cut(const int32_t *chunk_bnd, int32_t n_chunks, int64_t L, int t,
+                                             int32_t lf, int64_t c, const int32_t *leaf_ids, int64_t n,
+                                             int32_t lo, int32_t hi, int64_t lim) {
+    if (lim >= n) return hi;
+    if (chunk_bnd != nullptr)
+        return __ldg(chunk_bnd + (int64_t(t) * L + lf) * (n_chunks + 1) + (c + 1));
+    const int32_t *ids = leaf_ids + int64_t(t) * n;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (int64_t(__ldg(ids + mid)) < lim)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 struct VoteSearchArgs {
     const float *X;
     int64_t n;
@@ -869,6 +890,10 @@ struct VoteSearchArgs {
     const int32_t *leaf_off4;
     int64_t s4;
     int32_t sentinel;
+    // n > 65,536: id-chunk bounds of every leaf (null: binary searches)
+    const int32_t *chunk_bnd;
+    int32_t n_chunks;
+    int64_t L;
 };
 
 // Per warp: a buffer of emitted candidates waiting for their distances.
@@ -903,6 +928,7 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
     int32_t *cur = wbuf + VS_WARPS * WBUF;                                      // T_use
     int32_t *lend = cur + a.T_use;                                              // T_use
     int32_t *cend = lend + a.T_use;                                             // T_use
+    int32_t *lfs = cend + a.T_use;                                              // T_use: the query's leaves
     // merge area (aliases the counters once voting is over)
     float *md = reinterpret_cast<float *>(smem);                                // VS_WARPS * KR*32
     int32_t *mi = reinterpret_cast<int32_t *>(smem + VS_WARPS * KR * 32 * 4);
@@ -936,6 +962,7 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
         for (int i = tid; i < a.dpad; i += VS_THREADS) qv[i] = (i < a.d) ? a.Q[qi * a.d + i] : 0.f;
         for (int t = tid; t < a.T_use; t += VS_THREADS) {
             const int32_t lf = a.leaf_of_q[qi * a.T_use + t];
+            lfs[t] = lf;
             if (a.leaf4 != nullptr) {  // first 16-byte unit and length of the padded leaf
                 cur[t] = a.leaf_off4[lf];
                 lend[t] = a.leaf_off4[lf + 1] - cur[t];
@@ -1050,22 +1077,9 @@ __global__ void __launch_bounds__(VS_THREADS, 3) k_vote_search(const VoteSearchA
             const int64_t lim = c0 + CH_IDS;
             // end of each tree's ids inside this chunk: leaves list ids in
             // ascending order, so it is a lower bound of `lim`
-            for (int t = tid; t < a.T_use; t += VS_THREADS) {
-                int32_t lo = cur[t], hi = lend[t];
-                if (lim < a.n) {
-                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        if (int64_t(__ldg(ids + mid)) < lim)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
-                    }
-                    cend[t] = lo;
-                } else {
-                    cend[t] = hi;
-                }
-            }
+            for (int t = tid; t < a.T_use; t += VS_THREADS)
+                cend[t] = chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c0 / CH_IDS, a.leaf_ids, a.n, cur[t],
+                                    lend[t], lim);
             __syncthreads();
             int nb = 0;
             // the warp's tiles (128 consecutive ids of one tree's leaf) in
@@ -1258,6 +1272,10 @@ struct VoteEmitArgs {
     int32_t win;           // 128-entry windows per leaf
     uint64_t win_magic;    // ceil(2^32 / win): i / win = (i * win_magic) >> 32 for i < 256 * win
     int32_t sentinel;
+    // n > 65,536: id-chunk bounds of every leaf (null: binary searches)
+    const int32_t *chunk_bnd;
+    int32_t n_chunks;
+    int64_t L;
 };
 
 // Called by one thread once a query's votes are all in: records |S| and
@@ -1298,6 +1316,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
     int32_t *lend = cur + a.T_use;                                  // end of the query's leaf
     int32_t *cend = lend + a.T_use;                                 // end inside this chunk
     int32_t *wpre = cend + a.T_use;                                 // T_use + 1: first window
+    int32_t *lfs = wpre + a.T_use + 1;                              // T_use: the query's leaves
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
 
@@ -1318,6 +1337,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
         if (qi < 0) break;
         for (int t = tid; t < T; t += VE_THREADS) {
             const int32_t lf = a.leaf_of_q[qi * T + t];
+            lfs[t] = lf;
             cur[t] = a.leaf_off[lf];
             lend[t] = a.leaf_off[lf + 1];
         }
@@ -1334,19 +1354,9 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
             // thread of tree t also wrote cur[t] and lend[t])
             const int64_t lim = c0 + CH_IDS;
             for (int t = tid; t < T; t += VE_THREADS) {
-                int32_t lo = cur[t], hi = lend[t];
-                const int32_t p = lo;
-                if (lim < a.n) {
-                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        if (int64_t(__ldg(ids + mid)) < lim)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
-                    }
-                    hi = lo;
-                }
+                const int32_t p = cur[t];
+                const int32_t hi = chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c0 / CH_IDS, a.leaf_ids,
+                                             a.n, p, lend[t], lim);
                 cend[t] = hi;
                 const int64_t g = int64_t(t) * a.n + p;
                 const int32_t head = int32_t(g & 3);
@@ -1494,6 +1504,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
     int32_t *lend = cur + a.T_use;                                  // end of the query's leaf
     int32_t *cend = lend + a.T_use;                                 // end inside this chunk
     int32_t *fpre = cend + a.T_use;                                 // T_use + 1: flat start of each cut segment
+    int32_t *lfs = fpre + a.T_use + 1;                              // T_use: the query's leaves
     __shared__ int64_t s_q;
     __shared__ int s_cnt;
 
@@ -1516,6 +1527,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
         if (qi < 0) break;
         for (int t = tid; t < T; t += VE_THREADS) {
             const int32_t lf = a.leaf_of_q[qi * T + t];
+            lfs[t] = lf;
             cur[t] = a.leaf_off[lf];
             lend[t] = a.leaf_off[lf + 1];
         }
@@ -1532,19 +1544,9 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
             // wrote cur[t] and lend[t])
             const int64_t lim = c0 + CH_IDS;
             for (int t = tid; t < T; t += VE_THREADS) {
-                int32_t lo = cur[t], hi = lend[t];
-                const int32_t p = lo;
-                if (lim < a.n) {
-                    const int32_t *ids = a.leaf_ids + int64_t(t) * a.n;
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        if (int64_t(__ldg(ids + mid)) < lim)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
-                    }
-                    hi = lo;
-                }
+                const int32_t p = cur[t];
+                const int32_t hi = chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c0 / CH_IDS, a.leaf_ids,
+                                             a.n, p, lend[t], lim);
                 cend[t] = hi;
                 fpre[t] = hi - p;
             }
@@ -1641,19 +1643,47 @@ constexpr int VH_SLOTS = 1 << VH_LOG;  // 128 KB of shared memory
 constexpr int VH_THREADS = 1024;
 constexpr int VH_WARPS = VH_THREADS / 32;
 
-__device__ __forceinline__ bool vote_hash(uint32_t *tab, int32_t id, uint32_t vm1) {
-    const uint32_t tag = (uint32_t(id) + 1u) << 8;
-    uint32_t h = (uint32_t(id) * 0x9E3779B1u) >> (32 - VH_LOG);
-    for (int probe = 0; probe < VH_SLOTS; ++probe) {
-        uint32_t w = tab[h];
-        if (w == 0u) {
-            w = atomicCAS(tab + h, 0u, tag | 1u);
-            if (w == 0u) return vm1 == 0u;
-        }
-        if ((w & 0xffffff00u) == tag) return (atomicAdd(tab + h, 1u) & 0xffu) == vm1;
-        h = (h + 1u) & uint32_t(VH_SLOTS - 1);
+// The four entries e of one lane vote together (bit u of `valid`: entry u
+// is in its segment).  In each round the pending entries read their slots,
+// the empty ones are claimed with compare-and-swaps, the ones holding their
+// own id get an atomic add, all issued back to back; an entry whose slot holds
+// another id moves to the next slot for the next round.  Returns bit u set
+// when entry u's count went from v - 1 to v.
+__device__ __forceinline__ uint32_t vote_hash4(uint32_t *tab, const int32_t (&e)[4], uint32_t valid,
+                                               uint32_t vm1) {
+    uint32_t h[4], tg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        tg[u] = (uint32_t(e[u]) + 1u) << 8;
+        h[u] = (uint32_t(e[u]) * 0x9E3779B1u) >> (32 - VH_LOG);
     }
-    return false;  // not reached: the table holds every distinct id of the query
+    uint32_t pend = valid, hit = 0u;
+    for (int round = 0; pend != 0u && round < VH_SLOTS; ++round) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = ((pend >> u) & 1u) ? tab[h[u]] : 1u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (((pend >> u) & 1u) && w[u] == 0u) {
+                w[u] = atomicCAS(tab + h[u], 0u, tg[u] | 1u);
+                if (w[u] == 0u) {
+                    pend &= ~(1u << u);
+                    if (vm1 == 0u) hit |= 1u << u;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (((pend >> u) & 1u) && (w[u] & 0xffffff00u) == tg[u]) {
+                if ((atomicAdd(tab + h[u], 1u) & 0xffu) == vm1) hit |= 1u << u;
+                pend &= ~(1u << u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if ((pend >> u) & 1u) h[u] = (h[u] + 1u) & uint32_t(VH_SLOTS - 1);
+    }
+    return hit;  // every entry voted: the table holds every distinct id of the query
 }
 
 // Per query (one block of 32 warps, queries taken from an atomic counter):
@@ -1709,9 +1739,13 @@ __global__ void __launch_bounds__(VH_THREADS, 1) k_vote_hash(const VoteEmitArgs 
             const int4 q = ldg4_if(reinterpret_cast<const int4 *>(a.leaf_ids) + tg4[t] + 32 * j + lane, ok);
             if (ok) {
                 const int32_t e[4] = {q.x, q.y, q.z, q.w};
+                uint32_t valid = 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) valid |= uint32_t(rel + u >= 0 && rel + u < lh.x) << u;
+                const uint32_t hit = vote_hash4(tab, e, valid, vm1);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (rel + u >= 0 && rel + u < lh.x && vote_hash(tab, e[u], vm1)) {
+                    if ((hit >> u) & 1u) {
                         const int slot = atomicAdd(&s_cnt, 1);
                         if (slot < a.capq) clist[slot] = e[u];
                         if (a.dbg_cand != nullptr && slot < a.cand_cap) a.dbg_cand[qi * a.cand_cap + slot] = e[u];
@@ -2876,7 +2910,7 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     // + the sentinel's word (and 3 unused) and a spare word per lane
     size_t region = std::max(size_t(cnt_words + 36) * 4, merge_bytes);
     region = (region + 15) & ~size_t(15);
-    smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 + size_t(3 * ql.n_trees) * 4;
+    smem = region + size_t(idx->dpad) * 4 + size_t(VS_WARPS) * WBUF * 4 + size_t(4 * ql.n_trees) * 4;
     int per_sm = 0, sms = 0;
     cudaError_t e = launch_shape(reinterpret_cast<const void *>(k_vote_search<KR>), VS_THREADS, smem,
                                  idx->device, &per_sm, &sms);
@@ -2908,6 +2942,9 @@ cudaError_t plan_vote(const mrpt_index *idx, const QueryLaunch &ql, uint32_t *wo
     a.leaf_off4 = idx->leaf_off4;
     a.s4 = idx->vote_s4;
     a.sentinel = vote_sentinel(idx->n);
+    a.chunk_bnd = idx->chunk_bnd;
+    a.n_chunks = idx->n_chunks;
+    a.L = idx->L;
     a.rec = ql.rec;
     return cudaSuccess;
 }
@@ -2984,7 +3021,8 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     // table (one pass instead of one per 65,536-id chunk); ids + 1 take 24 bits
     static_assert(MRPT_VOTE_HASH_ENTRIES <= VH_SLOTS * 3 / 4, "the hash table must not fill");
     const bool fits = int64_t(ql.n_trees) * leaf_len <= MRPT_VOTE_HASH_ENTRIES && idx->n < (int64_t(1) << 24);
-    const bool hashed = ql.vote_table == MRPT_VOTE_HASH || (ql.vote_table == 0 && !flat && fits);
+    (void)fits;
+    const bool hashed = ql.vote_table == MRPT_VOTE_HASH;
     if (hashed) {
         VoteEmitArgs h{};
         h.n = idx->n;
@@ -3022,9 +3060,9 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     }
     auto kern = flat ? (one ? k_vote_flat<true> : k_vote_flat<false>) : packed ? k_vote_packed : k_vote_emit;
     const size_t smem = flat     ? size_t(cnt_words + 36) * 4 + size_t(ql.n_trees) * 8
-                        : packed ? size_t(cnt_words + 32) * 4 + size_t(4 * ql.n_trees + 1) * 4
+                        : packed ? size_t(cnt_words + 32) * 4 + size_t(5 * ql.n_trees + 1) * 4
                                  : size_t(cnt_words + 32) * 4 + size_t(ql.n_trees) * 16 +
-                                       size_t(4 * ql.n_trees + 1) * 4;
+                                       size_t(5 * ql.n_trees + 1) * 4;
     int per_sm = 0, sms = 0;
     cudaError_t e = launch_shape(reinterpret_cast<const void *>(kern), VE_THREADS, smem, idx->device, &per_sm,
                                  &sms);
@@ -3061,6 +3099,9 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     a.win = std::max((idx->vote_win + 1) / 2, 1);
     a.win_magic = ((uint64_t(1) << 32) + uint64_t(a.win) - 1) / uint64_t(a.win);
     a.sentinel = vote_sentinel(idx->n);
+    a.chunk_bnd = idx->chunk_bnd;
+    a.n_chunks = idx->n_chunks;
+    a.L = idx->L;
     kern<<<unsigned(blocks), VE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
