@@ -1325,6 +1325,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
     const int warp = tid >> 5;
     const uint32_t vm1 = uint32_t(a.v - 1);
     const int T = a.T_use;
+    int32_t next_cut = 0;  // thread t < T: tree t's cut of the next id chunk
 
     for (;;) {
         if (tid == 0) {
@@ -1353,10 +1354,18 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_emit(const VoteEmitArgs 
             // this chunk's part of every segment and its window count (the
             // thread of tree t also wrote cur[t] and lend[t])
             const int64_t lim = c0 + CH_IDS;
-            for (int t = tid; t < T; t += VE_THREADS) {
+            // thread t < T (T <= 255 < VE_THREADS) cuts tree t; with chunk
+            // bounds it loaded this cut during the previous chunk
+            if (tid < T) {
+                const int t = tid;
                 const int32_t p = cur[t];
-                const int32_t hi = chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c0 / CH_IDS, a.leaf_ids,
-                                             a.n, p, lend[t], lim);
+                const int64_t c = c0 / CH_IDS;
+                const int32_t hi = (a.chunk_bnd != nullptr && c > 0 && lim < a.n)
+                                       ? next_cut
+                                       : chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c, a.leaf_ids, a.n, p,
+                                                   lend[t], lim);
+                if (a.chunk_bnd != nullptr && lim + CH_IDS < a.n)
+                    next_cut = __ldg(a.chunk_bnd + (int64_t(t) * a.L + lfs[t]) * (a.n_chunks + 1) + (c + 2));
                 cend[t] = hi;
                 const int64_t g = int64_t(t) * a.n + p;
                 const int32_t head = int32_t(g & 3);
@@ -1513,6 +1522,7 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
     const int warp = tid >> 5;
     const uint32_t vm1 = uint32_t(a.v - 1);
     const int T = a.T_use;
+    int32_t next_cut = 0;  // thread t < T: tree t's cut of the next id chunk
     const uint32_t cnt_s = smem_u32(cnt);
     const uint32_t spare = 4u * uint32_t(a.cnt_words + lane);
 
@@ -1543,10 +1553,18 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
             // this chunk's part of every segment (the thread of tree t also
             // wrote cur[t] and lend[t])
             const int64_t lim = c0 + CH_IDS;
-            for (int t = tid; t < T; t += VE_THREADS) {
+            // thread t < T (T <= 255 < VE_THREADS) cuts tree t; with chunk
+            // bounds it loaded this cut during the previous chunk
+            if (tid < T) {
+                const int t = tid;
                 const int32_t p = cur[t];
-                const int32_t hi = chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c0 / CH_IDS, a.leaf_ids,
-                                             a.n, p, lend[t], lim);
+                const int64_t c = c0 / CH_IDS;
+                const int32_t hi = (a.chunk_bnd != nullptr && c > 0 && lim < a.n)
+                                       ? next_cut
+                                       : chunk_cut(a.chunk_bnd, a.n_chunks, a.L, t, lfs[t], c, a.leaf_ids, a.n, p,
+                                                   lend[t], lim);
+                if (a.chunk_bnd != nullptr && lim + CH_IDS < a.n)
+                    next_cut = __ldg(a.chunk_bnd + (int64_t(t) * a.L + lfs[t]) * (a.n_chunks + 1) + (c + 2));
                 cend[t] = hi;
                 fpre[t] = hi - p;
             }
