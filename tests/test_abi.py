@@ -104,3 +104,49 @@ def test_every_entry_point_cites_its_passage():
         seen.append(m.group(1))
         pos = m.end()
     assert set(seen) == set(declared_functions())
+
+
+def _c_layout(tmp_path, structs, macros):
+    """Compile a probe against include/mrpt.h with the host C compiler and
+    read back sizeof/offsetof of each struct field and the macro values."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mrpt.h"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    for mname in macros:
+        lines.append(f'  printf("macro {mname} %lld\\n", (long long)({mname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        a, b, c = ln.split()
+        got[(a, b)] = int(c)
+    return got
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of mrpt_build_opts, mrpt_query_opts and
+    mrpt_index_info have the C structs' field names, offsets and sizes, and
+    the binding's constants equal the header's macros: the C ABI passes these
+    structs and codes by layout and value only."""
+    import paper_1509_06957_gb300 as mr
+    mirrors = {"mrpt_build_opts": mr.BuildOpts, "mrpt_query_opts": mr.QueryOpts,
+               "mrpt_index_info": mr.IndexInfo}
+    structs = {c: [f[0] for f in py._fields_] for c, py in mirrors.items()}
+    macros = [n for n in dir(mr) if n.startswith("MRPT_") and isinstance(getattr(mr, n), int)]
+    got = _c_layout(tmp_path, structs, macros)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f in structs[cname]:
+            assert got[(cname, f)] == getattr(py, f).offset, f"{cname}.{f}"
+    for n in macros:
+        assert got[("macro", n)] == getattr(mr, n), n
