@@ -231,12 +231,18 @@ __global__ void k_gather_keys(const float *__restrict__ Pcm, int64_t n, int32_t 
     }
 }
 
+// WH (nodes of 16,384 points or more, 1,024-thread blocks): radix digits
+// are counted in one histogram per warp, a plain shared atomic per member,
+// summed after each pass; otherwise equal digits within a warp are
+// aggregated into one atomic on a single histogram.
+template <bool WH>
 __global__ void __launch_bounds__(1024) k_split_level(
     const float *__restrict__ Pcm, const uint32_t *__restrict__ okeys, int64_t n, int32_t l,
     int32_t level,
     const int32_t *__restrict__ perm_in, int32_t *__restrict__ perm_out,
     float *__restrict__ split, int64_t L) {
     __shared__ uint32_t hist[256];
+    __shared__ uint32_t whist[WH ? 32 * 256 : 1];  // per-warp digit counts (WH)
     __shared__ uint32_t s_bucket, s_count;
     __shared__ int64_t s_rank;
     __shared__ unsigned long long s_pivot;
@@ -266,25 +272,47 @@ __global__ void __launch_bounds__(1024) k_split_level(
     uint64_t prefix = 0, mask = 0;
     int64_t rank = (c + 1) / 2 - 1;
     bool unique = false;
+    constexpr bool per_warp = WH;
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
-        for (int i = tid; i < 256; i += bd) hist[i] = 0;
+        if constexpr (per_warp) {
+            for (int i = tid; i < nwarps * 256; i += bd) whist[i] = 0;
+        } else {
+            for (int i = tid; i < 256; i += bd) hist[i] = 0;
+        }
         __syncthreads();
-        for (int64_t base = 0; base < c; base += bd) {
-            const int64_t i = base + tid;
-            const bool in_seg = i < c;
-            uint32_t digit = 0;
-            bool hit = false;
-            if (in_seg) {
-                const uint64_t K = composite(i);
-                hit = (K & mask) == prefix;
-                digit = uint32_t(K >> shift) & 0xffu;
+        if constexpr (per_warp) {
+            uint32_t *wh = whist + warp * 256;
+            for (int64_t base = 0; base < c; base += bd) {
+                const int64_t i = base + tid;
+                if (i < c) {
+                    const uint64_t K = composite(i);
+                    if ((K & mask) == prefix) atomicAdd(wh + (uint32_t(K >> shift) & 0xffu), 1u);
+                }
             }
-            // warp-aggregated increment: one atomic per distinct digit
-            const unsigned act = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const unsigned peers = __match_any_sync(act, digit);
-                if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&hist[digit], __popc(peers));
+            __syncthreads();
+            for (int d = tid; d < 256; d += bd) {
+                uint32_t sum = 0;
+                for (int w = 0; w < nwarps; ++w) sum += whist[w * 256 + d];
+                hist[d] = sum;
+            }
+        } else {
+            for (int64_t base = 0; base < c; base += bd) {
+                const int64_t i = base + tid;
+                const bool in_seg = i < c;
+                uint32_t digit = 0;
+                bool hit = false;
+                if (in_seg) {
+                    const uint64_t K = composite(i);
+                    hit = (K & mask) == prefix;
+                    digit = uint32_t(K >> shift) & 0xffu;
+                }
+                // warp-aggregated increment: one atomic per distinct digit
+                const unsigned act = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    const unsigned peers = __match_any_sync(act, digit);
+                    if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&hist[digit], __popc(peers));
+                }
             }
         }
         __syncthreads();
@@ -354,16 +382,24 @@ __global__ void __launch_bounds__(1024) k_split_level(
             s_wr[warp] = __popc(rm);
         }
         __syncthreads();
-        uint32_t pl = 0, pr = 0, tl = 0, tr = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            const uint32_t a = s_wl[w], q = s_wr[w];
-            if (w < warp) {
-                pl += a;
-                pr += q;
+        // left / right counts of the warps before this one (pl, pr) and of
+        // the whole block (tl, tr): an inclusive scan of the per-warp counts
+        // across the lanes of every warp
+        const uint32_t a = lane < nwarps ? s_wl[lane] : 0u, q = lane < nwarps ? s_wr[lane] : 0u;
+        uint32_t ia = a, iq = q;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o);
+            const uint32_t yq = __shfl_up_sync(0xffffffffu, iq, o);
+            if (lane >= o) {
+                ia += ya;
+                iq += yq;
             }
-            tl += a;
-            tr += q;
         }
+        const uint32_t pl = __shfl_sync(0xffffffffu, ia - a, warp);
+        const uint32_t pr = __shfl_sync(0xffffffffu, iq - q, warp);
+        const uint32_t tl = __shfl_sync(0xffffffffu, ia, 31);
+        const uint32_t tr = __shfl_sync(0xffffffffu, iq, 31);
         if (valid) {
             // exactly nl composites are <= pivot (ids are unique), so both
             // destinations stay inside the node's segment; the bounds are
@@ -482,9 +518,13 @@ int grow_trees_device(mrpt_index *idx) {
             k_gather_keys<<<gblocks, 256, 0, s>>>(Pcm, n, l, j, T, perm_a, okeys);
             const int64_t blocks = int64_t(T) << j;
             // large nodes (few blocks) get 1,024 threads, small ones 256
-            const int threads = (n >> j) >= 16384 ? 1024 : 256;
-            k_split_level<<<dim3(unsigned(blocks)), threads, 0, s>>>(Pcm, okeys, n, l, j, perm_a,
-                                                                   perm_b, idx->split, L);
+            const bool large = (n >> j) >= 16384;
+            if (large)
+                k_split_level<true><<<dim3(unsigned(blocks)), 1024, 0, s>>>(Pcm, okeys, n, l, j, perm_a, perm_b,
+                                                                           idx->split, L);
+            else
+                k_split_level<false><<<dim3(unsigned(blocks)), 256, 0, s>>>(Pcm, okeys, n, l, j, perm_a, perm_b,
+                                                                           idx->split, L);
             e = cudaGetLastError();
             std::swap(perm_a, perm_b);
         }
