@@ -1647,8 +1647,9 @@ __global__ void __launch_bounds__(VE_THREADS, 3) k_vote_packed(const VoteEmitArg
     }
 }
 
-// Hashed vote counters (n > 65,536 with every query's T leaves holding at
-// most VH_SLOTS * 3 / 4 entries): one pass per query, no id chunks.  The
+// Hashed vote counters, on request (mrpt_query_opts.vote_table; every
+// query's T leaves must hold at most 3/4 VH_SLOTS entries): one pass per
+// query, no id chunks.  The
 // table is VH_SLOTS 32-bit words in shared memory, a word (id + 1) << 8 |
 // count, 0 when empty; an id's slot is found by a multiplicative hash and
 // linear probing.  The T leaves hold at most 3/4 VH_SLOTS entries, so at
@@ -3035,11 +3036,11 @@ cudaError_t launch_vote_emit(const mrpt_index *idx, const QueryLaunch &ql, cudaS
     // ceil(size / 4) (the vote layout pads with the sentinel)
     const int64_t min_units = (idx->n / idx->L + 3) / 4;
     const bool one = flat && (idx->vote_win + 1) / 2 <= 1 && min_units >= 32;
-    // hashed counters when the T leaves of a query hold at most 3/4 of the
-    // table (one pass instead of one per 65,536-id chunk); ids + 1 take 24 bits
+    // hashed counters only on request: the caller (mrpt_query_ex, plan
+    // creation) checked that the T leaves of a query hold at most
+    // MRPT_VOTE_HASH_ENTRIES entries and that ids + 1 take 24 bits.  The
+    // id-chunked counters measured faster where both apply.
     static_assert(MRPT_VOTE_HASH_ENTRIES <= VH_SLOTS * 3 / 4, "the hash table must not fill");
-    const bool fits = int64_t(ql.n_trees) * leaf_len <= MRPT_VOTE_HASH_ENTRIES && idx->n < (int64_t(1) << 24);
-    (void)fits;
     const bool hashed = ql.vote_table == MRPT_VOTE_HASH;
     if (hashed) {
         VoteEmitArgs h{};
